@@ -1,0 +1,110 @@
+"""Target images of the synthetic scenes (oracle, FP64).  Test infrastructure only.
+
+The paper trains on real WorldView-3 images (Sec. 5.1), not available here.
+Stand-in: a heightfield surface z = h(x, y) (synth.heightfield) seen by the
+synthetic cameras.  The colour of a pixel is the Lambertian shading of the
+first surface point its ray hits:
+    colour = albedo(x, y) * (0.2 + 0.8 max(0, n . s))
+with n the unit normal (-dh/dx, -dh/dy, 1)/|.|, s the sun direction and
+albedo the bilinear interpolation of the 32 x 32 colour noise over the scene's
+xy box.  The hit is found by marching the ray from z_max in steps of at most
+`step` metres of height and refining the first sign change of
+z(t) - h(x(t), y(t)) by bisection to 1e-9 m.  Rays that reach z_min or leave
+the box without a hit get colour 0.
+"""
+import numpy as np
+
+from synth import pack_pixel
+from .camera import rays_fp64
+
+
+def height(hf, x, y):
+    z = np.full_like(x, hf.z_base)
+    for a, k, p in zip(hf.amp, hf.k, hf.phase):
+        z = z + a * np.sin(2 * np.pi * (k[0] * x + k[1] * y) + p)
+    return z
+
+
+def height_grad(hf, x, y):
+    gx = np.zeros_like(x)
+    gy = np.zeros_like(y)
+    for a, k, p in zip(hf.amp, hf.k, hf.phase):
+        c = a * 2 * np.pi * np.cos(2 * np.pi * (k[0] * x + k[1] * y) + p)
+        gx = gx + c * k[0]
+        gy = gy + c * k[1]
+    return gx, gy
+
+
+def albedo(hf, x, y):
+    g = hf.albedo.shape[0]
+    u = np.clip((x - hf.lo[0]) / (hf.hi[0] - hf.lo[0]), 0, 1) * (g - 1)
+    v = np.clip((y - hf.lo[1]) / (hf.hi[1] - hf.lo[1]), 0, 1) * (g - 1)
+    i0 = np.minimum(np.floor(v).astype(int), g - 2)
+    j0 = np.minimum(np.floor(u).astype(int), g - 2)
+    fv = (v - i0)[:, None]
+    fu = (u - j0)[:, None]
+    A = hf.albedo
+    return (A[i0, j0] * (1 - fv) * (1 - fu) + A[i0 + 1, j0] * fv * (1 - fu)
+            + A[i0, j0 + 1] * (1 - fv) * fu + A[i0 + 1, j0 + 1] * fv * fu)
+
+
+def shade_rays(hf, top, d, step=1.0):
+    """Colour (n, 3) of rays starting at `top` (scene coordinates, z = z_max)
+    with unit directions d, against heightfield hf inside its box."""
+    n = top.shape[0]
+    z_len = hf.hi[2] - hf.lo[2]
+    t_max = z_len / np.maximum(-d[:, 2], 1e-12)
+    n_steps = int(np.ceil(z_len / step))
+    f_prev = top[:, 2] - height(hf, top[:, 0], top[:, 1])
+    t_prev = np.zeros(n)
+    hit_lo = np.full(n, np.nan)
+    hit_hi = np.full(n, np.nan)
+    found = f_prev <= 0
+    hit_lo[found] = 0.0
+    hit_hi[found] = 0.0
+    for k in range(1, n_steps + 1):
+        t = t_max * (k / n_steps)
+        p = top + t[:, None] * d
+        f = p[:, 2] - height(hf, p[:, 0], p[:, 1])
+        new = (~found) & (f <= 0)
+        hit_lo[new] = t_prev[new]
+        hit_hi[new] = t[new]
+        found |= new
+        t_prev = t
+    lo = hit_lo[found]
+    hi = hit_hi[found]
+    tp = top[found]
+    dd = d[found]
+    for _ in range(200):
+        if lo.size == 0 or np.max(hi - lo) <= 1e-9:
+            break
+        mid = 0.5 * (lo + hi)
+        p = tp + mid[:, None] * dd
+        f = p[:, 2] - height(hf, p[:, 0], p[:, 1])
+        below = f <= 0
+        hi = np.where(below, mid, hi)
+        lo = np.where(below, lo, mid)
+    out = np.zeros((n, 3))
+    if lo.size:
+        p = tp + hi[:, None] * dd
+        inside = ((p[:, 0] >= hf.lo[0]) & (p[:, 0] <= hf.hi[0]) & (p[:, 1] >= hf.lo[1]) & (p[:, 1] <= hf.hi[1]))
+        gx, gy = height_grad(hf, p[:, 0], p[:, 1])
+        nrm = np.stack([-gx, -gy, np.ones_like(gx)], 1)
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        lam = 0.2 + 0.8 * np.maximum(0.0, nrm @ hf.sun)
+        col = albedo(hf, p[:, 0], p[:, 1]) * lam[:, None]
+        out[np.flatnonzero(found)] = np.where(inside[:, None], col, 0.0)
+    return out
+
+
+def render_targets(hf, cameras, step=1.0):
+    """Float32 crop images (h, w, 3), one per camera."""
+    imgs = []
+    for vi, cam in enumerate(cameras):
+        r0, c0, h, w = cam.crop
+        rr, cc = np.meshgrid(np.arange(r0, r0 + h), np.arange(c0, c0 + w), indexing="ij")
+        pix = pack_pixel(np.full(rr.size, vi), rr.ravel(), cc.ravel())
+        o, d = rays_fp64(cameras, pix, np.zeros(3), hf.lo[2], hf.hi[2])
+        col = shade_rays(hf, o, d, step)
+        imgs.append(col.reshape(h, w, 3).astype(np.float32))
+    return imgs

@@ -1,0 +1,174 @@
+"""Pins of the oracle's hash-grid encoding (NGP, Sec. 4.1) and MLPs against
+closed forms, exact adjoints and finite differences (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle import hashgrid, mlp
+
+
+def test_level_layouts_of_the_workloads():
+    lay = hashgrid.layout(16, 2, 19, 16, 2048)
+    assert lay.res[0] == 16 and lay.res[-1] == 2048
+    assert list(np.flatnonzero(lay.dense)) == [0, 1, 2, 3, 4]    # 5 dense, 11 hashed levels
+    assert np.all(lay.size[lay.dense] >= (lay.res[lay.dense] + 1) ** 3)
+    assert np.all(lay.size[~lay.dense] == 1 << 19)
+    assert np.all(lay.size % 8 == 0)
+    assert lay.offset[0] == 0 and np.all(np.diff(lay.offset) == lay.size[:-1])
+    lay1 = hashgrid.layout(8, 2, 14, 16, 256)
+    assert lay1.res[-1] == 256 and lay1.dense.sum() == 2
+    # geometric growth b = (N_max / N_min)^(1/(L-1)) within the floor
+    b = (2048 / 16) ** (1 / 15)
+    assert np.all(np.abs(lay.res - 16 * b ** np.arange(16)) < 1.0)
+
+
+def test_spatial_hash_known_values():
+    T = 1 << 19
+    for (x, y, z) in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (3, 5, 7), (2047, 1, 2048), (4000, 4001, 4002)]:
+        expect = ((x * 1) % 2 ** 32 ^ (y * 2654435761) % 2 ** 32 ^ (z * 805459861) % 2 ** 32) % T
+        got = hashgrid.corner_index(np.array([x]), np.array([y]), np.array([z]), 0, False, T)[0]
+        assert got == expect
+
+
+def _trilinear_field(rng):
+    c = rng.normal(size=8)
+
+    def f(x, y, z):
+        return (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * y + c[5] * x * z + c[6] * y * z
+                + c[7] * x * y * z)
+    return f
+
+
+def test_dense_levels_reproduce_trilinear_fields_exactly():
+    """Table = f(vertex / N) with f trilinear => encode(x) = f(x) at dense levels."""
+    lay = hashgrid.layout(3, 2, 16, 4, 20)
+    assert lay.dense.all()
+    rng = np.random.default_rng(0)
+    fs = [[_trilinear_field(rng) for _ in range(2)] for _ in range(3)]
+    table = np.zeros((lay.n_entries, 2))
+    for l in range(3):
+        N = int(lay.res[l])
+        v = np.arange(N + 1)
+        X, Y, Z = np.meshgrid(v, v, v, indexing="ij")
+        idx = lay.offset[l] + X + Y * (N + 1) + Z * (N + 1) ** 2     # x fastest
+        for f in range(2):
+            table[idx.ravel(), f] = fs[l][f](X.ravel() / N, Y.ravel() / N, Z.ravel() / N)
+    xyz = rng.uniform(0, 1, (500, 3)).astype(np.float32)
+    xyz[:5] = [[0, 0, 0], [1, 1, 1], [0.5, 0.25, 1], [1, 0, 0.75], [0.125, 1, 0]]
+    out = hashgrid.encode(xyz, table, lay)
+    for l in range(3):
+        # the level evaluates the field at its binary32 grid coordinate g = fl(x N), i.e. at g / N
+        N = int(lay.res[l])
+        x64 = (xyz * np.float32(N)).astype(np.float32).astype(np.float64) / N
+        assert np.max(np.abs(x64 - xyz)) < 1e-6
+        for f in range(2):
+            assert np.max(np.abs(out[:, 2 * l + f] - fs[l][f](x64[:, 0], x64[:, 1], x64[:, 2]))) < 1e-12
+
+
+def test_hashed_levels_interpolate_the_eight_hashed_corners():
+    """At a hashed level every feature is a convex combination (weights sum to 1)
+    of the entries at the 8 hashed corners; a table that is 1 everywhere
+    encodes to 1, and one-hot tables give the corner weights."""
+    lay = hashgrid.layout(2, 2, 6, 8, 30)
+    assert not lay.dense[1]
+    rng = np.random.default_rng(1)
+    xyz = rng.uniform(0, 1, (200, 3)).astype(np.float32)
+    out = hashgrid.encode(xyz, np.ones((lay.n_entries, 2)), lay)
+    assert np.allclose(out, 1.0, atol=1e-13)
+    idx, w = hashgrid.corners(xyz, lay, 1)
+    assert np.allclose(w.sum(1), 1.0, atol=1e-14) and np.all(w >= 0)
+    assert np.all((idx >= lay.offset[1]) & (idx < lay.offset[1] + lay.size[1]))
+
+
+def test_cell_decision_at_vertices_and_upper_face():
+    i, frac = hashgrid.cells(np.array([[0.0, 1.0, 0.5]], np.float32), 16)
+    assert list(i[0]) == [0, 15, 8] and list(frac[0]) == [0.0, 1.0, 0.0]
+
+
+def test_encode_backward_is_the_exact_adjoint():
+    """<encode(table), dfeat> == <table, encode_backward(dfeat)> for any table,
+    colliding hashed entries included."""
+    lay = hashgrid.layout(4, 2, 8, 4, 64)
+    rng = np.random.default_rng(2)
+    xyz = rng.uniform(0, 1, (300, 3)).astype(np.float32)
+    table = rng.normal(size=(lay.n_entries, 2))
+    dfeat = rng.normal(size=(300, lay.L * 2))
+    lhs = np.sum(hashgrid.encode(xyz, table, lay) * dfeat)
+    rhs = np.sum(table * hashgrid.encode_backward(xyz, dfeat, lay))
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+
+
+def _mlp_params(rng, in_dim, hidden, G, colour):
+    geo = [rng.normal(size=(hidden, in_dim)) * 0.5, rng.normal(size=(hidden, hidden)) * 0.3,
+           rng.normal(size=(G, hidden)) * 0.3]
+    col = [rng.normal(size=(hidden, G)) * 0.5, rng.normal(size=(hidden, hidden)) * 0.3,
+           rng.normal(size=(3, hidden)) * 0.3] if colour else None
+    return geo, col
+
+
+def test_mlp_hand_computable_case():
+    """W1 copies features, W2 the identity, W3 picks hidden unit 0 for g_0 and
+    units 1..3 for g_1..3: sigma = exp(relu(x0)), rgb = sigmoid(relu(x1..3))."""
+    x = np.array([[0.3, -0.2, 0.7, 1.5], [-1.0, 2.0, 0.0, -0.5]])
+    W1 = np.zeros((8, 4))
+    W1[:4, :4] = np.eye(4)
+    W2 = np.eye(8)
+    W3 = np.zeros((4, 8))
+    W3[:, :4] = np.eye(4)
+    sigma, rgb, _ = mlp.forward(x, [W1, W2, W3], None)
+    r = np.maximum(x, 0)
+    assert np.allclose(sigma, np.exp(r[:, 0]), rtol=1e-15)
+    assert np.allclose(rgb, 1 / (1 + np.exp(-r[:, 1:4])), rtol=1e-15)
+
+
+@pytest.mark.parametrize("colour", [False, True])
+def test_mlp_backward_matches_central_differences(colour):
+    rng = np.random.default_rng(4)
+    G = 16 if colour else 4
+    geo, col = _mlp_params(rng, 8, 12, G, colour)
+    x = rng.normal(size=(40, 8))
+    ds = rng.normal(size=40)
+    dr = rng.normal(size=(40, 3))
+
+    def f(geo_, col_, x_):
+        s, c, _ = mlp.forward(x_, geo_, col_)
+        return np.sum(ds * s) + np.sum(dr * c)
+
+    _, _, acts = mlp.forward(x, geo, col)
+    dgeo, dcol, dx = mlp.backward(ds, dr, geo, col, acts)
+    mats = [("g", k) for k in range(3)] + ([("c", k) for k in range(3)] if colour else [])
+    for kind, k in mats:
+        W = geo[k] if kind == "g" else col[k]
+        an = dgeo[k] if kind == "g" else dcol[k]
+        for (a, b) in [(0, 0), (1, 2), (W.shape[0] - 1, W.shape[1] - 1), (2, 1)]:
+            if a >= W.shape[0] or b >= W.shape[1]:
+                continue
+            h = 1e-6 * max(1.0, abs(W[a, b]))
+            old = W[a, b]
+            W[a, b] = old + h
+            fp = f(geo, col, x)
+            W[a, b] = old - h
+            fm = f(geo, col, x)
+            W[a, b] = old
+            fd = (fp - fm) / (2 * h)
+            assert abs(fd - an[a, b]) <= 1e-6 * max(1.0, abs(fd))
+    for (i, j) in [(0, 0), (5, 3), (39, 7)]:
+        h = 1e-6
+        xp = x.copy()
+        xp[i, j] += h
+        xm = x.copy()
+        xm[i, j] -= h
+        fd = (f(geo, col, xp) - f(geo, col, xm)) / (2 * h)
+        assert abs(fd - dx[i, j]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_truncated_exponential_gradient():
+    """d sigma / d g_0 = exp(clamp(g_0, -15, 15)): beyond 15 the gradient stops growing."""
+    W1 = np.zeros((2, 1))
+    W1[0, 0] = 1.0
+    W2 = np.eye(2)
+    W3 = np.zeros((4, 2))
+    W3[0, 0] = 1.0
+    x = np.array([[3.0], [20.0]])
+    _, _, acts = mlp.forward(x, [W1, W2, W3], None)
+    dgeo, _, dx = mlp.backward(np.ones(2), np.zeros((2, 3)), [W1, W2, W3], None, acts)
+    assert np.allclose(dx[:, 0], [np.exp(3.0), np.exp(15.0)], rtol=1e-14)
