@@ -1,0 +1,278 @@
+/*
+ * snk.h - C ABI of libsnk, the B300 (sm_103a) training step of a Snake-NeRF
+ * tile or 2x2 tile window ("Tile and Slide", Billouard et al., ICCV 2025).
+ *
+ * One step: rays from satellite cameras (Sec. 3, Sec. 4.6 "On-the-fly Ray
+ * Calculation") -> window acceptance and segmented sampling (Sec. 4.4, 4.5)
+ * -> multiresolution hash encoding per tile (Sec. 4.1, NGP) -> local density
+ * MLP and shared colour MLP (Sec. 4.1) -> volume rendering (NeRF Eq. 3,
+ * Sec. 4.5) -> colour loss, backward and Adam (Sec. 4.4, 4.6).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status (SNK_OK = 0 or an SNK_ERR_* code);
+ *    snk_last_error() gives a message for the last failing call on a context.
+ *    Invalid arguments are reported before anything is launched.
+ *  - Data pointers are DEVICE pointers owned by the caller unless a
+ *    parameter says "host".  The library never frees caller memory.  The
+ *    context owns only its workspace (snk_ctx_reserve) and its copy of the
+ *    views (snk_set_views); snk_ctx_destroy frees both.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default
+ *    stream) unless they return a host value.  A call that needs more
+ *    workspace than reserved grows it with cudaMalloc, which synchronises the
+ *    device; reserve first to keep calls asynchronous and capturable.
+ *  - Floating point is binary32 unless stated; the camera model is evaluated
+ *    in binary64.  Discrete results (acceptance, segment bounds, sample
+ *    counts and offsets, hash indices) follow a fixed sequence of IEEE
+ *    operations and are reproducible bit for bit.
+ *  - Sample arrays are SLOT-MAJOR: the samples of parameter slot k occupy
+ *    [slot_base[k], slot_base[k] + slot_count[k]) and slot_base[k] is a
+ *    multiple of 128.  Inside a slot, the samples of a ray segment are
+ *    contiguous and ordered along the ray; segments appear in ray order.
+ *    Padding entries between slots are never read as samples.
+ *
+ * Parameter layout (flat, per model):
+ *    [slot 0 | ... | slot n-1 | colour block(s)]
+ *    slot block   = hash table (n_entries x F, entry-major) | W1 | W2 | W3
+ *    colour block = V1 | V2 | V3          (matrices row-major [out][in])
+ *  with n_entries, offsets and sizes given by snk_model_layout().
+ */
+#ifndef SNK_H
+#define SNK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *snk_stream_t; /* a cudaStream_t */
+typedef struct snk_ctx snk_ctx;
+
+enum {
+    SNK_OK = 0,
+    SNK_ERR_INVALID_ARG = 1,  /* bad descriptor, size or NULL pointer */
+    SNK_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    SNK_ERR_OOM = 3,          /* workspace allocation failed */
+    SNK_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    SNK_ERR_DEVICE_CHECK = 5, /* a device-side bounds or capacity check fired */
+    SNK_ERR_OVERFLOW = 6      /* non-finite gradients: Adam step skipped, loss scale halved */
+};
+
+/* Camera kinds (Sec. 4.3 names the RPC model; affine is its linear case). */
+enum { SNK_CAM_AFFINE = 0, SNK_CAM_RPC3 = 1 };
+/* Precision of a model. */
+enum { SNK_FP32 = 0, SNK_MIXED = 1 };
+
+/* One view: its localisation map (r, c, h) -> (x, y) and its resident crop.
+ *  AFFINE: x = a0 + a1 c + a2 r + a3 h, y = b0 + b1 c + b2 r + b3 h.
+ *  RPC3:   with rn = (r - off[0]) / scale[0], cn = (c - off[1]) / scale[1],
+ *          hn = (h - off[2]) / scale[2]:
+ *          x = off[3] + scale[3] * Nx / Dx,  y = off[4] + scale[4] * Ny / Dy,
+ *          Nx, Dx, Ny, Dy = coef[0..3] . m(cn, rn, hn), the 20 cubic monomials
+ *          1, c, r, h, cr, ch, rh, c^2, r^2, h^2, crh, c^3, cr^2, ch^2, c^2 r,
+ *          r^3, rh^2, c^2 h, r^2 h, h^3 (each a left-to-right product, the sum
+ *          taken left to right).
+ *  (r, c) are full-image pixel coordinates; pixel (row, col) is sampled at its
+ *  centre (row + 0.5, col + 0.5).  The crop (crop_r0, crop_c0, crop_h, crop_w)
+ *  is the part of the image whose target colours are resident (Sec. 4.3). */
+typedef struct {
+    int32_t kind;
+    int32_t width, height;
+    int32_t crop_r0, crop_c0, crop_h, crop_w;
+    int32_t reserved;
+    double a[4], b[4];
+    double off[5], scale[5];
+    double coef[4][20];
+} snk_camera;
+
+/* A window of nx x ny loaded tiles (nx, ny in {1, 2}) inside a scene box
+ * (Sec. 4.2, 4.4).  Scene-metre boxes; all tiles share z_min = origin[2] and
+ * height tile_size[2].  slot[iy * nx + ix] is the parameter slot of tile
+ * (ix, iy), a permutation of 0..nx*ny-1. */
+typedef struct {
+    double origin[3];
+    double tile_size[3];
+    double scene_lo[3], scene_hi[3];
+    int32_t nx, ny;
+    int32_t slot[4];
+} snk_window;
+
+/* Model sizes.  Grid: L levels of F = 2 features, T = 2^log2_T entries,
+ * resolutions n_min .. n_max (NGP).  Density MLP: L*F -> 64 -> 64 -> geo_out
+ * (ReLU hidden, no biases).  geo_out = 4 without a colour net (rgb =
+ * sigmoid(g1..3)); geo_out = 16 with a colour MLP 16 -> 64 -> 64 -> 3,
+ * shared by all slots (shared_colour = 1, the paper's global colour network)
+ * or one per slot.  Supported: L*F in {8, 16, 32}, hidden = 64, n_slots 1..4. */
+typedef struct {
+    int32_t L, F, log2_T, n_min, n_max;
+    int32_t hidden;
+    int32_t geo_out;
+    int32_t colour;
+    int32_t shared_colour;
+    int32_t n_slots;
+    int32_t precision; /* SNK_FP32 or SNK_MIXED */
+} snk_model;
+
+/* Layout facts computed from a model on the host (no GPU needed). */
+typedef struct {
+    int32_t res[32];           /* N_l */
+    int32_t dense[32];         /* 1 if (N_l + 1)^3 <= T */
+    int64_t level_offset[32];  /* first entry of level l */
+    int64_t level_size[32];    /* entries of level l (multiple of 8) */
+    int64_t n_entries;         /* entries per table */
+    int64_t grid_params;       /* n_entries * F */
+    int64_t tile_params;       /* one slot block */
+    int64_t colour_params;     /* one colour block */
+    int64_t n_params;          /* whole flat vector */
+    int32_t n_optimisers;      /* slots + colour blocks */
+    int32_t n_colour_blocks;
+} snk_layout;
+
+/* Sampler: samples per segment K = clamp(rint(K_ray len_seg / len_ray),
+ * K_min, K_max); render = 1 puts every sample at its bin centre. */
+typedef struct {
+    int32_t K_ray, K_min, K_max;
+    int32_t render;
+    uint32_t seed;
+    uint32_t iteration; /* Philox key word; the training step uses its own counter */
+} snk_sampler;
+
+/* Adam hyper-parameters (I-NGP's: 1e-2, 0.9, 0.99, 1e-15, 1e-6). */
+typedef struct {
+    float lr, beta1, beta2, eps, l2_mlp;
+} snk_adam;
+
+/* Trainable state, all device memory of n_params entries (snk_layout). */
+typedef struct {
+    float *params;       /* binary32 master weights */
+    uint16_t *params_lp; /* SNK_MIXED: working copy, FP16 for tables, BF16 for MLP weights; else NULL */
+    float *grads;        /* gradient accumulator; must be zero before a step, zeroed by the step */
+    float *adam_m;
+    float *adam_v;
+    int32_t *adam_step;  /* n_optimisers step counts (device), incremented by each step */
+} snk_params;
+
+/* Per-step device state (caller-owned device memory, zero-initialise once,
+ * then set loss_scale; the step updates it). */
+typedef struct {
+    float loss;          /* MSE of the last step */
+    float loss_scale;    /* dynamic loss scale (SNK_MIXED); 1 for SNK_FP32 */
+    uint32_t n_accepted; /* accepted rays of the last step */
+    uint32_t n_samples;  /* samples of the last step */
+    uint32_t status;     /* bit 0: overflow skip, bit 1: device check, bit 2: timeout */
+    int32_t good_steps;  /* consecutive finite steps (loss-scale growth) */
+    uint32_t iteration;  /* step counter, Philox key word of the stratified jitter */
+    uint32_t slot_base[5];
+    uint32_t slot_count[4];
+    uint32_t reserved[3];
+} snk_state;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (made current).  *out is NULL on error. */
+int snk_ctx_create(int device, snk_ctx **out);
+/* Free the context and its workspace (synchronises the device).  NULL is a no-op. */
+int snk_ctx_destroy(snk_ctx *ctx);
+/* Size the workspace for batches of up to max_rays rays and max_samples samples. */
+int snk_ctx_reserve(snk_ctx *ctx, int64_t max_rays, int64_t max_samples);
+/* Message of the last failing call on ctx (static storage of the context). */
+const char *snk_last_error(const snk_ctx *ctx);
+/* Library version string (host, static). */
+const char *snk_version(void);
+
+/* Host only: grid level resolutions/offsets and parameter counts (NGP, Sec. 4.1).
+ * Returns SNK_ERR_INVALID_ARG for unsupported sizes.  Needs no GPU. */
+int snk_model_layout(const snk_model *model, snk_layout *out);
+
+/* Copy n_views cameras (host array) and per-view crop pointers (host array of
+ * device pointers to crop_h x crop_w x 3 binary32 images, or NULL when no
+ * targets are needed) into the context.  Asynchronous on `stream` through
+ * context-owned pinned staging memory; the host arrays may be reused after
+ * the call returns.  Sec. 4.3 (crops), Sec. 4.6 (rays from the cameras). */
+int snk_set_views(snk_ctx *ctx, const snk_camera *cams, int n_views, const float *const *crops,
+                  snk_stream_t stream);
+
+/* ---- stages ----------------------------------------------------------- */
+
+/* Rays, acceptance, segments and stratified samples for B packed pixel ids
+ * pix[i] = view << 24 | row << 12 | col (Sec. 4.4, 4.5, 4.6).
+ * Outputs (device, caller-allocated):
+ *   ray_od    [6][B]   o.x, o.y, o.z, d.x, d.y, d.z (window-local metres, unit d)
+ *   ray_ok    [B]      1 if accepted
+ *   seg_slot  [B][3]   slot of each segment, 255 if unused
+ *   seg_t     [B][3][2] t0, t1 of each segment
+ *   seg_n     [B][3]   samples per segment (0 if unused)
+ *   seg_off   [B][3]   first sample of each segment in the slot-major arrays
+ *   smp_t, smp_dt [cap], smp_xyz [cap][3] (tile-local [0,1]^3)
+ *   state     device snk_state: n_accepted, n_samples, slot_base, slot_count
+ * cap = capacity of the sample arrays; if the slot-major extent exceeds it,
+ * no sample is written and status bit 1 is set (SNK_ERR_DEVICE_CHECK from
+ * snk_sync_status).  A pixel whose view does not exist is rejected with the
+ * same status bit.  Jitter: Philox-4x32-10 (Salmon et al. 2011), key
+ * (seed, iteration), counter (ray, j >> 2, 1, 0), lane j & 3, j = index of
+ * the sample along its ray. */
+int snk_sample_segments(snk_ctx *ctx, const snk_window *win, const uint32_t *pix, int B,
+                        const snk_sampler *sampler, float *ray_od, uint8_t *ray_ok, uint8_t *seg_slot,
+                        float *seg_t, uint32_t *seg_n, uint32_t *seg_off, float *smp_t, float *smp_dt,
+                        float *smp_xyz, int64_t cap, snk_state *state, snk_stream_t stream);
+
+/* Hash encoding (Sec. 4.1, NGP) of S slot-major samples: feat [S][L*F]
+ * binary32, level-major.  Samples outside the slot ranges of `state` are
+ * skipped.  idx_out (nullable) [S][L][8] receives the table entry index of
+ * each corner (within the slot's table) for bit-exact checks. */
+int snk_encode(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *smp_xyz,
+               const snk_state *state, int64_t S, float *feat, uint32_t *idx_out, snk_stream_t stream);
+/* Adds dfeat [S][L*F] scattered with the trilinear weights into p->grads (tables). */
+int snk_encode_backward(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *smp_xyz,
+                        const snk_state *state, int64_t S, const float *dfeat, snk_stream_t stream);
+
+/* Density + colour MLPs (Sec. 4.1) on features feat [S][L*F]:
+ * out [S][4] = (sigma, r, g, b). */
+int snk_mlp(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *feat,
+            const snk_state *state, int64_t S, float *out, snk_stream_t stream);
+/* Backward of snk_mlp for upstream dout [S][4] = (dsigma, dr, dg, db): adds the
+ * weight gradients into p->grads and writes dfeat [S][L*F]. */
+int snk_mlp_backward(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *feat,
+                     const snk_state *state, int64_t S, const float *dout, float *dfeat, snk_stream_t stream);
+
+/* Volume rendering (NeRF Eq. 3, Sec. 4.5) of B rays from slot-major samples
+ * (sigma_rgb [S][4], smp_t, smp_dt) reached through seg_n / seg_off:
+ * out [B][5] = (r, g, b, depth, opacity), t_final [B] (nullable). */
+int snk_composite(snk_ctx *ctx, const float *sigma_rgb, const float *smp_t, const float *smp_dt,
+                  const uint32_t *seg_n, const uint32_t *seg_off, int B, float *out, float *t_final,
+                  snk_stream_t stream);
+/* Backward of snk_composite for per-ray colour gradients g_rgb [B][3]:
+ * d_sigma_rgb [S][4] = (dsigma, dr, dg, db) for every sample of the rays. */
+int snk_composite_backward(snk_ctx *ctx, const float *sigma_rgb, const float *smp_t, const float *smp_dt,
+                           const uint32_t *seg_n, const uint32_t *seg_off, int B, const float *g_rgb,
+                           float *d_sigma_rgb, snk_stream_t stream);
+
+/* ---- whole step --------------------------------------------------------- */
+
+/* One training step on B packed pixels (Sec. 4.4, last paragraph): rays,
+ * segments, samples (jitter key = (sampler->seed, state->iteration)), encode,
+ * MLPs, rendering, MSE loss over accepted rays against the views' crops,
+ * backward, Adam per optimiser (slot tables + density MLP; colour net), then
+ * state->iteration += 1.  SNK_MIXED adds dynamic loss scaling: a step with
+ * non-finite gradients is skipped (status bit 0) and the scale halved.
+ * Optional outputs (nullable): out [B][5] rendered (r, g, b, depth, opacity).
+ * Never synchronises; read state (device) for loss and counts. */
+int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
+                   const snk_sampler *sampler, const snk_adam *adam, const snk_params *p, snk_state *state,
+                   float *out, snk_stream_t stream);
+
+/* Render B packed pixels (forward only, bin-centre samples): out [B][5]. */
+int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
+               const snk_sampler *sampler, const snk_params *p, snk_state *state, float *out,
+               snk_stream_t stream);
+
+/* Wait for `stream` and report device-side status bits of `state` as a
+ * status code (SNK_ERR_DEVICE_CHECK, SNK_ERR_TIMEOUT, SNK_ERR_OVERFLOW). */
+int snk_sync_status(snk_ctx *ctx, const snk_state *state, snk_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNK_H */

@@ -1,0 +1,132 @@
+// Shared device-side definitions of libsnk (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "../../include/snk.h"
+
+namespace snk {
+
+constexpr int kHidden = 64;
+constexpr int kMaxSlots = 4;
+constexpr int kMaxViews = 256;
+constexpr int kMaxLevels = 32;
+constexpr int kSlotAlign = 128;   // slot-major sample ranges start on multiples of this
+constexpr uint32_t kStatusOverflow = 1u;
+constexpr uint32_t kStatusCheck = 2u;
+constexpr uint32_t kStatusTimeout = 4u;
+
+// Camera of one view as the kernels see it (binary64 coefficients).
+struct DevView {
+  int32_t kind, width, height, crop_r0, crop_c0, crop_h, crop_w, pad;
+  double a[4], b[4];
+  double off[5], scale[5];
+  double coef[4][20];
+  const float *crop;  // crop_h x crop_w x 3 binary32, or nullptr
+};
+
+// Window constants.  The binary32 values are the correctly rounded images of
+// the binary64 descriptor (computed on the host), so that every discrete
+// decision is a fixed IEEE binary32 sequence.
+struct WinParams {
+  double origin[3];
+  double z_min, z_max;
+  float win_hi[3];       // nx*Wt, ny*Ht, Z (window-local)
+  float scene_lo[3], scene_hi[3];
+  float split[2];        // interior planes x = Wt, y = Ht
+  float inv_size[3];     // 1/Wt, 1/Ht, 1/Z
+  int32_t nx, ny;
+  int32_t slot[4];
+  int32_t n_slots;
+};
+
+struct SamplerParams {
+  int32_t K_ray, K_min, K_max, render;
+  uint32_t seed, iteration;
+  int32_t use_state_iteration;  // 1: the jitter key's second word is state->iteration
+};
+
+// Grid level table passed by value to kernels.
+struct GridParams {
+  int32_t L, F, log2_T, T;
+  int32_t res[kMaxLevels];
+  int32_t dense[kMaxLevels];
+  uint32_t offset[kMaxLevels];
+};
+
+// ---- exact binary32 / binary64 arithmetic (never contracted) --------------
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// ---- Philox-4x32-10 (Salmon et al. 2011) ---------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Uniform (x >> 8) * 2^-24, exact in binary32.
+__device__ __forceinline__ float u32_to_unit(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-08f; }
+
+// Stratified jitter of sample j of ray `ray`: counter (ray, j >> 2, 1, 0), lane j & 3.
+__device__ __forceinline__ float jitter(uint32_t seed, uint32_t iteration, uint32_t ray, uint32_t j) {
+  const uint4 r = philox4x32_10(make_uint4(ray, j >> 2, 1u, 0u), make_uint2(seed, iteration));
+  const uint32_t lane = j & 3u;
+  const uint32_t x = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+  return u32_to_unit(x);
+}
+
+// ---- NGP dense index / spatial hash ----------------------------------------
+__device__ __forceinline__ uint32_t grid_index(uint32_t x, uint32_t y, uint32_t z, int N, bool dense, uint32_t Tmask) {
+  if (dense) {
+    const uint32_t n1 = (uint32_t)N + 1u;
+    return x + y * n1 + z * n1 * n1;
+  }
+  return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & Tmask;
+}
+
+// Cell of one axis at resolution N: g = x * N (binary32), i = min(floor(g), N - 1), frac = g - i.
+__device__ __forceinline__ void grid_cell(float x, int N, int &i, float &frac) {
+  const float g = fmul(x, (float)N);
+  int c = (int)floorf(g);
+  c = c < N - 1 ? c : N - 1;
+  c = c > 0 ? c : 0;
+  i = c;
+  frac = fsub(g, (float)c);
+}
+
+// Slot of a slot-major sample index; -1 for padding.
+__device__ __forceinline__ int slot_of(const snk_state *st, int64_t s) {
+#pragma unroll
+  for (int k = 0; k < kMaxSlots; ++k) {
+    const int64_t b = st->slot_base[k];
+    if (s >= b && s < b + (int64_t)st->slot_count[k]) return k;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void set_status(snk_state *st, uint32_t bit) { atomicOr(&st->status, bit); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace snk

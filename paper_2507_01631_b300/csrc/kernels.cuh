@@ -1,0 +1,93 @@
+// Internal interfaces between the translation units of libsnk.
+#pragma once
+#include "common.cuh"
+
+namespace snk {
+
+// Workspace of one ray batch (context-owned, or caller buffers for the stage API).
+struct RayBuffers {
+  float *ray_od;       // [6][B]
+  uint8_t *ray_ok;     // [B]
+  uint8_t *seg_slot;   // [B][3]
+  float *seg_t;        // [B][3][2]
+  uint32_t *seg_n;     // [B][3]
+  uint32_t *seg_off;   // [B][3]
+  uint32_t *cnt;       // [5][B]  per-slot sample counts, row 4 = accepted flag
+  uint32_t *excl;      // [5][B]  exclusive scans of cnt within a scan block
+  uint32_t *block_tot; // [5][nb] scan block totals, then bases
+  float *smp_t;        // [cap]
+  float *smp_dt;       // [cap]
+  float *smp_xyz;      // [cap][3]
+};
+
+int scan_blocks(int B);
+cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinParams &win, const SamplerParams &smp,
+                                   const uint32_t *pix, int B, int need_targets, const RayBuffers &rb, int64_t cap,
+                                   snk_state *state, cudaStream_t st);
+
+// Everything a field kernel needs to know about a model.
+struct ModelDev {
+  GridParams grid;
+  int32_t in_dim, geo_out, colour, shared_colour, n_slots, mixed;
+  int64_t tile_params, grid_params, colour_params, colour_base;
+  int64_t w1, w2, w3;  // offsets of the density-MLP matrices inside a slot block
+  int64_t v1, v2, v3;  // offsets of the colour-MLP matrices inside a colour block
+};
+
+enum FieldMode { kEncodeOnly = 0, kForward = 1, kBackward = 2 };
+
+struct FieldArgs {
+  ModelDev m;
+  const float *params;        // binary32 master weights
+  const uint16_t *params_lp;  // FP16 tables / BF16 MLP working copy (mixed)
+  float *grads;
+  const float *xyz;           // [S][3] tile-local sample positions
+  const float *feat_in;       // [S][IN] features instead of encoding (MLP-only API), or null
+  float *feat_out;            // [S][IN] encoded features (encode API), or null
+  uint32_t *idx_out;          // [S][L][8] corner entries (encode API), or null
+  float *sigma_rgb;           // forward output [S][4]
+  const float *dsr;           // backward input [S][4]
+  float *dfeat_out;           // backward: write dfeat here instead of scattering, or null
+  const snk_state *state;
+  int64_t S;                  // extent of the slot-major arrays
+  int32_t slot_only;          // -1: every slot; k: only slot k (per-tile launches)
+  int32_t mode;
+};
+cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st);
+cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st);
+
+struct CompositeArgs {
+  const float *sigma_rgb;
+  const float *smp_t;
+  const float *smp_dt;
+  const uint32_t *seg_n;
+  const uint32_t *seg_off;
+  int32_t B;
+  float *out;             // [B][5] or null
+  float *t_final;         // [B] or null
+  const float *g_rgb;     // [B][3] upstream gradient (stage API), or null
+  const uint32_t *pix;    // training: pixels for the targets
+  const DevView *views;
+  float *dsr;             // [S][4] backward output, or null (forward only)
+  snk_state *state;
+  int32_t train;          // 1: MSE loss against targets, gradient scaled by the loss scale
+};
+cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st);
+
+struct AdamArgs {
+  float *params;
+  uint16_t *params_lp;
+  float *grads;
+  float *m;
+  float *v;
+  int32_t *steps;
+  int64_t n;
+  int32_t n_groups;
+  int64_t start[9], end[9], mlp_start[9];
+  float lr, beta1, beta2, eps, l2;
+  snk_state *state;
+  int32_t mixed;
+};
+cudaError_t launch_adam(const AdamArgs &a, int sm_count, cudaStream_t st);
+
+}  // namespace snk

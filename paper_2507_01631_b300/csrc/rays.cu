@@ -1,0 +1,358 @@
+// S1 + S2: on-the-fly rays from satellite cameras, window acceptance, segment
+// split, samples per segment, slot-major sample offsets and stratified sample
+// placement.  Sec. 3 / 4.6 ("On-the-fly Ray Calculation": rays are computed
+// when needed, never stored for whole images), Sec. 4.4 (accept only rays
+// whose tiles are all loaded), Sec. 4.5 (per-tile near/far pairs; each
+// segment is sampled on its own so that its ends fall on tile faces).
+//
+// Every value that decides something discrete is a fixed sequence of IEEE
+// operations written with explicit round-to-nearest intrinsics (no fused
+// multiply-add): binary64 for the camera, binary32 for the box clipping,
+// the segment bounds, the per-segment sample counts and the sample positions.
+#include "kernels.cuh"
+
+namespace snk {
+
+// ---- camera (binary64) -----------------------------------------------------
+__device__ __forceinline__ double rpc_poly(const double *k, double c, double r, double h) {
+  // monomials 1, c, r, h, cr, ch, rh, c^2, r^2, h^2, crh, c^3, cr^2, ch^2, c^2 r,
+  // r^3, rh^2, c^2 h, r^2 h, h^3; products left to right, sum left to right.
+  const double cc = dmul(c, c), rr = dmul(r, r), hh = dmul(h, h);
+  double s = k[0];
+  s = dadd(s, dmul(k[1], c));
+  s = dadd(s, dmul(k[2], r));
+  s = dadd(s, dmul(k[3], h));
+  s = dadd(s, dmul(k[4], dmul(c, r)));
+  s = dadd(s, dmul(k[5], dmul(c, h)));
+  s = dadd(s, dmul(k[6], dmul(r, h)));
+  s = dadd(s, dmul(k[7], cc));
+  s = dadd(s, dmul(k[8], rr));
+  s = dadd(s, dmul(k[9], hh));
+  s = dadd(s, dmul(k[10], dmul(dmul(c, r), h)));
+  s = dadd(s, dmul(k[11], dmul(cc, c)));
+  s = dadd(s, dmul(k[12], dmul(c, rr)));
+  s = dadd(s, dmul(k[13], dmul(c, hh)));
+  s = dadd(s, dmul(k[14], dmul(cc, r)));
+  s = dadd(s, dmul(k[15], dmul(rr, r)));
+  s = dadd(s, dmul(k[16], dmul(r, hh)));
+  s = dadd(s, dmul(k[17], dmul(cc, h)));
+  s = dadd(s, dmul(k[18], dmul(rr, h)));
+  s = dadd(s, dmul(k[19], dmul(hh, h)));
+  return s;
+}
+
+__device__ __forceinline__ void localise(const DevView &v, double row, double col, double h, double &x, double &y) {
+  if (v.kind == SNK_CAM_AFFINE) {
+    x = dadd(dadd(dadd(v.a[0], dmul(v.a[1], col)), dmul(v.a[2], row)), dmul(v.a[3], h));
+    y = dadd(dadd(dadd(v.b[0], dmul(v.b[1], col)), dmul(v.b[2], row)), dmul(v.b[3], h));
+    return;
+  }
+  const double rn = ddiv(dsub(row, v.off[0]), v.scale[0]);
+  const double cn = ddiv(dsub(col, v.off[1]), v.scale[1]);
+  const double hn = ddiv(dsub(h, v.off[2]), v.scale[2]);
+  x = dadd(v.off[3], dmul(v.scale[3], ddiv(rpc_poly(v.coef[0], cn, rn, hn), rpc_poly(v.coef[1], cn, rn, hn))));
+  y = dadd(v.off[4], dmul(v.scale[4], ddiv(rpc_poly(v.coef[2], cn, rn, hn), rpc_poly(v.coef[3], cn, rn, hn))));
+}
+
+// ---- slab clip (binary32) ----------------------------------------------------
+struct Slab {
+  float t_in, t_out;
+};
+
+__device__ __forceinline__ Slab slab(const float o[3], const float d[3], const float inv[3], const float lo[3],
+                                     const float hi[3]) {
+  float tn[3], tf[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] == 0.0f) {
+      const bool inside = o[a] >= lo[a] && o[a] <= hi[a];
+      tn[a] = inside ? -INFINITY : INFINITY;
+      tf[a] = inside ? INFINITY : -INFINITY;
+    } else {
+      const float t1 = fmul(fsub(lo[a], o[a]), inv[a]);
+      const float t2 = fmul(fsub(hi[a], o[a]), inv[a]);
+      tn[a] = fminf(t1, t2);
+      tf[a] = fmaxf(t1, t2);
+    }
+  }
+  Slab s;
+  s.t_in = fmaxf(fmaxf(fmaxf(0.0f, tn[0]), tn[1]), tn[2]);
+  s.t_out = fminf(fminf(tf[0], tf[1]), tf[2]);
+  return s;
+}
+
+// One thread per ray: camera -> (o, d) -> acceptance -> <= 3 segments -> K per segment.
+__global__ void k_rays(const DevView *__restrict__ views, int n_views, WinParams win, SamplerParams smp,
+                       const uint32_t *__restrict__ pix, int B, int need_targets, float *__restrict__ ray_od,
+                       uint8_t *__restrict__ ray_ok, uint8_t *__restrict__ seg_slot, float *__restrict__ seg_t,
+                       uint32_t *__restrict__ seg_n, uint32_t *__restrict__ cnt, snk_state *state) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) {
+    state->loss = 0.0f;
+    state->reserved[0] = 0u;  // non-finite-gradient flag of this step
+  }
+  if (r >= B) return;
+  const uint32_t p = pix[r];
+  const int v = (int)(p >> 24), row = (int)((p >> 12) & 0xFFFu), col = (int)(p & 0xFFFu);
+  bool valid = v < n_views;
+  if (valid && need_targets) {
+    const DevView &cv = views[v];
+    valid = cv.crop != nullptr && row >= cv.crop_r0 && row < cv.crop_r0 + cv.crop_h && col >= cv.crop_c0 &&
+            col < cv.crop_c0 + cv.crop_w;
+  }
+  float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, -1.f};
+  if (valid) {
+    const DevView &cv = views[v];
+    const double rr = dadd((double)row, 0.5), cc = dadd((double)col, 0.5);
+    double xt, yt, xb, yb;
+    localise(cv, rr, cc, win.z_max, xt, yt);
+    localise(cv, rr, cc, win.z_min, xb, yb);
+    const double Dx = dsub(xb, xt), Dy = dsub(yb, yt), Dz = dsub(win.z_min, win.z_max);
+    const double n = __dsqrt_rn(dadd(dadd(dmul(Dx, Dx), dmul(Dy, Dy)), dmul(Dz, Dz)));
+    o[0] = __double2float_rn(dsub(xt, win.origin[0]));
+    o[1] = __double2float_rn(dsub(yt, win.origin[1]));
+    o[2] = __double2float_rn(dsub(win.z_max, win.origin[2]));
+    d[0] = __double2float_rn(ddiv(Dx, n));
+    d[1] = __double2float_rn(ddiv(Dy, n));
+    d[2] = __double2float_rn(ddiv(Dz, n));
+  } else {
+    set_status(state, kStatusCheck);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ray_od[(size_t)a * B + r] = o[a];
+    ray_od[(size_t)(3 + a) * B + r] = d[a];
+  }
+  float inv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) inv[a] = d[a] == 0.0f ? INFINITY : fdiv(1.0f, d[a]);
+  const float zero3[3] = {0.f, 0.f, 0.f};
+  const Slab sc = slab(o, d, inv, win.scene_lo, win.scene_hi);
+  const Slab wn = slab(o, d, inv, zero3, win.win_hi);
+  const bool ok = valid && sc.t_in < sc.t_out && wn.t_in <= sc.t_in && sc.t_out <= wn.t_out;
+
+  uint8_t s_slot[3] = {255, 255, 255};
+  float s_t0[3] = {0.f, 0.f, 0.f}, s_t1[3] = {0.f, 0.f, 0.f};
+  uint32_t s_n[3] = {0u, 0u, 0u};
+  if (ok) {
+    const float a = sc.t_in, b = sc.t_out;
+    float cut[2] = {0.f, 0.f};
+    int nc = 0;
+    if (win.nx == 2 && d[0] != 0.0f) {
+      const float tp = fmul(fsub(win.split[0], o[0]), inv[0]);
+      if (a < tp && tp < b) cut[nc++] = tp;
+    }
+    if (win.ny == 2 && d[1] != 0.0f) {
+      const float tp = fmul(fsub(win.split[1], o[1]), inv[1]);
+      if (a < tp && tp < b) cut[nc++] = tp;
+    }
+    if (nc == 2 && cut[1] < cut[0]) {
+      const float tmp = cut[0];
+      cut[0] = cut[1];
+      cut[1] = tmp;
+    }
+    float bnd[4] = {a, b, b, b};
+    if (nc >= 1) bnd[1] = cut[0];
+    if (nc == 2) bnd[2] = cut[1];
+    bnd[1 + nc] = b;
+    const float len_ray = fsub(b, a);
+    int ns = 0;
+    for (int j = 0; j < nc + 1; ++j) {
+      const float lo_t = bnd[j], hi_t = bnd[j + 1];
+      const float len = fsub(hi_t, lo_t);
+      if (!(len > 0.0f)) continue;
+      const float mid = fadd(lo_t, fmul(len, 0.5f));
+      const int ix = (win.nx == 2 && fadd(o[0], fmul(mid, d[0])) > win.split[0]) ? 1 : 0;
+      const int iy = (win.ny == 2 && fadd(o[1], fmul(mid, d[1])) > win.split[1]) ? 1 : 0;
+      const float q = fdiv(len, len_ray);
+      const float kf = fmul((float)smp.K_ray, q);
+      int k = (int)rintf(kf);
+      k = k < smp.K_min ? smp.K_min : k;
+      k = k > smp.K_max ? smp.K_max : k;
+      s_slot[ns] = (uint8_t)win.slot[iy * win.nx + ix];
+      s_t0[ns] = lo_t;
+      s_t1[ns] = hi_t;
+      s_n[ns] = (uint32_t)k;
+      ++ns;
+    }
+  }
+  ray_ok[r] = ok ? 1 : 0;
+  uint32_t c[kMaxSlots] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    seg_slot[(size_t)r * 3 + s] = s_slot[s];
+    seg_t[((size_t)r * 3 + s) * 2 + 0] = s_t0[s];
+    seg_t[((size_t)r * 3 + s) * 2 + 1] = s_t1[s];
+    seg_n[(size_t)r * 3 + s] = s_n[s];
+    if (s_slot[s] < kMaxSlots) c[s_slot[s]] += s_n[s];
+  }
+  for (int k = 0; k < win.n_slots; ++k) cnt[(size_t)k * B + r] = c[k];
+  cnt[(size_t)kMaxSlots * B + r] = ok ? 1u : 0u;  // accepted-ray counter rides along as row 4
+}
+
+// ---- per-slot exclusive scan over rays ---------------------------------------
+// Row k of cnt (k < n_slots) holds ray r's samples in slot k; row 4 the accepted flag.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanChunk = kScanThreads * kScanPer;
+
+__global__ void k_scan_local(const uint32_t *__restrict__ cnt, int B, int n_slots, uint32_t *__restrict__ excl,
+                             uint32_t *__restrict__ block_tot) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  const int row = (int)blockIdx.y < n_slots ? (int)blockIdx.y : kMaxSlots;  // rows 0..n_slots-1, then 4
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+  uint32_t v[kScanPer];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    v[i] = (base + i < B) ? cnt[(size_t)row * B + base + i] : 0u;
+    sum += v[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    warp_tot[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = inc - sum + (warp > 0 ? warp_tot[warp - 1] : 0u);
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    if (base + i < B) excl[(size_t)row * B + base + i] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == kScanThreads - 1) block_tot[(size_t)row * gridDim.x + blockIdx.x] = warp_tot[31];
+}
+
+// One block, one warp per row: scan the block totals of every row, place the
+// slot ranges (each starting on a multiple of kSlotAlign), count accepted rays,
+// check the sample capacity.
+__global__ void k_scan_top(uint32_t *__restrict__ block_tot, int nb, int n_slots, int64_t cap, snk_state *state) {
+  __shared__ uint32_t tot[kMaxSlots + 1];
+  const int row = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (row < n_slots || row == kMaxSlots) {
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      const int b = b0 + lane;
+      const uint32_t v = b < nb ? block_tot[(size_t)row * nb + b] : 0u;
+      uint32_t inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (b < nb) block_tot[(size_t)row * nb + b] = carry + inc - v;  // exclusive block base
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) tot[row] = carry;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t base = 0;
+    uint32_t n = 0;
+    for (int k = 0; k < kMaxSlots; ++k) {
+      const uint32_t c = k < n_slots ? tot[k] : 0u;
+      state->slot_base[k] = (uint32_t)base;
+      state->slot_count[k] = c;
+      n += c;
+      base += c;
+      base = (base + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+    }
+    state->slot_base[kMaxSlots] = (uint32_t)base;
+    state->n_accepted = tot[kMaxSlots];
+    if ((int64_t)base > cap || base > 0xFFFFFFFFull) {
+      set_status(state, kStatusCheck);
+      for (int k = 0; k < kMaxSlots; ++k) state->slot_count[k] = 0u;
+      state->slot_base[kMaxSlots] = 0u;
+      state->n_samples = 0u;
+    } else {
+      state->n_samples = n;
+    }
+  }
+}
+
+// Warp per ray: segment offsets, then t, delta and tile-local xyz of every sample.
+__global__ void k_samples(const float *__restrict__ ray_od, const uint8_t *__restrict__ seg_slot,
+                          const float *__restrict__ seg_t, const uint32_t *__restrict__ seg_n,
+                          const uint32_t *__restrict__ excl, const uint32_t *__restrict__ block_tot, int nb, int B,
+                          WinParams win, SamplerParams smp, const snk_state *__restrict__ state,
+                          uint32_t *__restrict__ seg_off, float *__restrict__ smp_t, float *__restrict__ smp_dt,
+                          float *__restrict__ smp_xyz) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int r = warp;
+  const uint32_t iteration = smp.use_state_iteration ? state->iteration : smp.iteration;
+  float o[3], d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o[a] = ray_od[(size_t)a * B + r];
+    d[a] = ray_od[(size_t)(3 + a) * B + r];
+  }
+  uint32_t j0 = 0;
+  for (int s = 0; s < 3; ++s) {
+    const int k = seg_slot[(size_t)r * 3 + s];
+    const uint32_t n = seg_n[(size_t)r * 3 + s];
+    uint32_t off = 0;
+    const bool live = k < kMaxSlots && n > 0 && state->slot_count[k] > 0;
+    if (live) off = state->slot_base[k] + block_tot[(size_t)k * nb + r / kScanChunk] + excl[(size_t)k * B + r];
+    if (lane == 0) seg_off[(size_t)r * 3 + s] = off;
+    if (!live) continue;
+    int tile = 0;
+    for (int q = 0; q < win.nx * win.ny; ++q)
+      if (win.slot[q] == k) tile = q;
+    const int ix = tile % win.nx, iy = tile / win.nx;
+    const float lo[3] = {ix ? win.split[0] : 0.0f, iy ? win.split[1] : 0.0f, 0.0f};
+    const float t0 = seg_t[((size_t)r * 3 + s) * 2 + 0], t1 = seg_t[((size_t)r * 3 + s) * 2 + 1];
+    const float w = fdiv(fsub(t1, t0), (float)n);
+    for (uint32_t i = lane; i < n; i += 32) {
+      const float u = smp.render ? 0.5f : jitter(smp.seed, iteration, (uint32_t)r, j0 + i);
+      const float t = fadd(t0, fmul(fadd((float)i, u), w));
+      const size_t q = (size_t)off + i;
+      smp_t[q] = t;
+      smp_dt[q] = w;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float p = fadd(o[a], fmul(t, d[a]));
+        float l = fmul(fsub(p, lo[a]), win.inv_size[a]);
+        l = fminf(fmaxf(l, 0.0f), 1.0f);
+        smp_xyz[q * 3 + a] = l;
+      }
+    }
+    j0 += n;
+  }
+}
+
+// ---- host launcher -------------------------------------------------------------
+int scan_blocks(int B) { return (B + kScanChunk - 1) / kScanChunk; }
+
+cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinParams &win, const SamplerParams &smp,
+                                   const uint32_t *pix, int B, int need_targets, const RayBuffers &rb, int64_t cap,
+                                   snk_state *state, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  k_rays<<<(B + 255) / 256, 256, 0, st>>>(views, n_views, win, smp, pix, B, need_targets, rb.ray_od, rb.ray_ok,
+                                          rb.seg_slot, rb.seg_t, rb.seg_n, rb.cnt, state);
+  const int nb = scan_blocks(B);
+  const dim3 g(nb, win.n_slots + 1);
+  k_scan_local<<<g, kScanThreads, 0, st>>>(rb.cnt, B, win.n_slots, rb.excl, rb.block_tot);
+  k_scan_top<<<1, 32 * (kMaxSlots + 1), 0, st>>>(rb.block_tot, nb, win.n_slots, cap, state);
+  const int64_t threads = (int64_t)B * 32;
+  k_samples<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n, rb.excl,
+                                                                rb.block_tot, nb, B, win, smp, state, rb.seg_off,
+                                                                rb.smp_t, rb.smp_dt, rb.smp_xyz);
+  return cudaGetLastError();
+}
+
+}  // namespace snk
