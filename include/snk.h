@@ -181,6 +181,11 @@ int snk_ctx_reserve(snk_ctx *ctx, int64_t max_rays, int64_t max_samples);
 const char *snk_last_error(const snk_ctx *ctx);
 /* Library version string (host, static). */
 const char *snk_version(void);
+/* Host only: sizeof of the ABI structs, in the order snk_camera, snk_window,
+ * snk_model, snk_layout, snk_sampler, snk_adam, snk_params, snk_state, written
+ * to sizes[0..n-1] (n <= 8).  Lets a binding check its struct mirrors.  Returns
+ * the number written. */
+int snk_abi_sizes(int64_t *sizes, int n);
 
 /* Host only: grid level resolutions/offsets and parameter counts (NGP, Sec. 4.1).
  * Returns SNK_ERR_INVALID_ARG for unsupported sizes.  Needs no GPU. */
@@ -188,9 +193,9 @@ int snk_model_layout(const snk_model *model, snk_layout *out);
 
 /* Copy n_views cameras (host array) and per-view crop pointers (host array of
  * device pointers to crop_h x crop_w x 3 binary32 images, or NULL when no
- * targets are needed) into the context.  Asynchronous on `stream` through
- * context-owned pinned staging memory; the host arrays may be reused after
- * the call returns.  Sec. 4.3 (crops), Sec. 4.6 (rays from the cameras). */
+ * targets are needed) into the context.  Set-up call: it synchronises
+ * `stream`, so the host arrays may be reused after it returns.  At most 256
+ * views.  Sec. 4.3 (crops), Sec. 4.6 (rays from the cameras). */
 int snk_set_views(snk_ctx *ctx, const snk_camera *cams, int n_views, const float *const *crops,
                   snk_stream_t stream);
 

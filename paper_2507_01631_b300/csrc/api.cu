@@ -1,0 +1,644 @@
+// C ABI of libsnk: context and workspace, argument validation, host-side
+// model layout, and the order of the kernels of one training step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "kernels.cuh"
+
+struct snk_ctx {
+  int device = 0;
+  int sm_count = 148;
+  char err[512] = {0};
+  int64_t cap_rays = 0, cap_samples = 0;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  snk::RayBuffers rb{};
+  float *sigma_rgb = nullptr;  // [cap_samples][4]
+  float *dsr = nullptr;        // [cap_samples][4]
+  snk::DevView *d_views = nullptr;
+  snk::DevView *h_views = nullptr;  // pinned staging
+  int n_views = 0;
+};
+
+namespace {
+
+using namespace snk;
+
+int fail(snk_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define SNK_CK(ctx, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(ctx, SNK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int layout_of(const snk_model *m, snk_layout *o, char *msg, size_t msg_len) {
+  auto bad = [&](const char *why) {
+    snprintf(msg, msg_len, "invalid model: %s", why);
+    return SNK_ERR_INVALID_ARG;
+  };
+  if (!m || !o) return bad("NULL pointer");
+  if (m->L < 1 || m->L > kMaxLevels) return bad("L must be in 1..32");
+  if (m->F != 2) return bad("F must be 2");
+  const int in = m->L * m->F;
+  if (in != 8 && in != 16 && in != 32) return bad("L*F must be 8, 16 or 32");
+  if (m->log2_T < 4 || m->log2_T > 24) return bad("log2_T must be in 4..24");
+  if (m->n_min < 2 || m->n_max < m->n_min || m->n_max > 4095) return bad("need 2 <= n_min <= n_max < 4096");
+  if (m->hidden != kHidden) return bad("hidden must be 64");
+  if (m->colour != 0 && m->colour != 1) return bad("colour must be 0 or 1");
+  if (m->geo_out != (m->colour ? 16 : 4)) return bad("geo_out must be 16 with a colour MLP, 4 without");
+  if (m->shared_colour != 0 && m->shared_colour != 1) return bad("shared_colour must be 0 or 1");
+  if (m->n_slots < 1 || m->n_slots > kMaxSlots) return bad("n_slots must be in 1..4");
+  if (m->precision != SNK_FP32 && m->precision != SNK_MIXED) return bad("precision must be SNK_FP32 or SNK_MIXED");
+  memset(o, 0, sizeof(*o));
+  const int64_t T = (int64_t)1 << m->log2_T;
+  const double b = m->L > 1 ? std::exp((std::log((double)m->n_max) - std::log((double)m->n_min)) / (m->L - 1)) : 1.0;
+  int64_t off = 0;
+  for (int l = 0; l < m->L; ++l) {
+    const int64_t res = (int64_t)std::floor((double)m->n_min * std::pow(b, (double)l) + 1e-6);
+    const int64_t nv = (res + 1) * (res + 1) * (res + 1);
+    const bool dense = nv <= T;
+    int64_t size = dense ? nv : T;
+    size = (size + 7) / 8 * 8;
+    o->res[l] = (int32_t)res;
+    o->dense[l] = dense ? 1 : 0;
+    o->level_offset[l] = off;
+    o->level_size[l] = size;
+    off += size;
+  }
+  o->n_entries = off;
+  o->grid_params = off * m->F;
+  const int64_t geo = (int64_t)kHidden * in + (int64_t)kHidden * kHidden + (int64_t)m->geo_out * kHidden;
+  o->tile_params = o->grid_params + geo;
+  o->colour_params = m->colour ? (int64_t)kHidden * m->geo_out + (int64_t)kHidden * kHidden + 3 * kHidden : 0;
+  o->n_colour_blocks = m->colour ? (m->shared_colour ? 1 : m->n_slots) : 0;
+  o->n_params = m->n_slots * o->tile_params + o->n_colour_blocks * o->colour_params;
+  o->n_optimisers = m->n_slots + o->n_colour_blocks;
+  return SNK_OK;
+}
+
+ModelDev model_dev(const snk_model *m, const snk_layout &lay) {
+  ModelDev d{};
+  d.grid.L = m->L;
+  d.grid.F = m->F;
+  d.grid.log2_T = m->log2_T;
+  d.grid.T = 1 << m->log2_T;
+  for (int l = 0; l < m->L; ++l) {
+    d.grid.res[l] = lay.res[l];
+    d.grid.dense[l] = lay.dense[l];
+    d.grid.offset[l] = (uint32_t)lay.level_offset[l];
+  }
+  d.in_dim = m->L * m->F;
+  d.geo_out = m->geo_out;
+  d.colour = m->colour;
+  d.shared_colour = m->shared_colour;
+  d.n_slots = m->n_slots;
+  d.mixed = m->precision == SNK_MIXED;
+  d.tile_params = lay.tile_params;
+  d.grid_params = lay.grid_params;
+  d.colour_params = lay.colour_params;
+  d.colour_base = (int64_t)m->n_slots * lay.tile_params;
+  d.w1 = lay.grid_params;
+  d.w2 = d.w1 + (int64_t)kHidden * d.in_dim;
+  d.w3 = d.w2 + (int64_t)kHidden * kHidden;
+  d.v1 = 0;
+  d.v2 = (int64_t)kHidden * m->geo_out;
+  d.v3 = d.v2 + (int64_t)kHidden * kHidden;
+  return d;
+}
+
+int check_window(snk_ctx *ctx, const snk_window *w, int n_slots, WinParams *o) {
+  if (!w) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
+  if ((w->nx != 1 && w->nx != 2) || (w->ny != 1 && w->ny != 2))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "window nx, ny must be 1 or 2");
+  if (w->nx * w->ny != n_slots)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "window has %d tiles but the model has %d slots", w->nx * w->ny, n_slots);
+  int seen = 0;
+  for (int q = 0; q < n_slots; ++q) {
+    if (w->slot[q] < 0 || w->slot[q] >= n_slots || (seen >> w->slot[q]) & 1)
+      return fail(ctx, SNK_ERR_INVALID_ARG, "window slot[] must be a permutation of 0..%d", n_slots - 1);
+    seen |= 1 << w->slot[q];
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (!(w->tile_size[a] > 0.0)) return fail(ctx, SNK_ERR_INVALID_ARG, "tile_size must be positive");
+    if (!(w->scene_hi[a] > w->scene_lo[a])) return fail(ctx, SNK_ERR_INVALID_ARG, "scene box is empty");
+  }
+  memset(o, 0, sizeof(*o));
+  for (int a = 0; a < 3; ++a) o->origin[a] = w->origin[a];
+  o->z_min = w->origin[2];
+  o->z_max = w->origin[2] + w->tile_size[2];
+  o->win_hi[0] = (float)(w->nx * w->tile_size[0]);
+  o->win_hi[1] = (float)(w->ny * w->tile_size[1]);
+  o->win_hi[2] = (float)w->tile_size[2];
+  for (int a = 0; a < 3; ++a) {
+    o->scene_lo[a] = (float)(w->scene_lo[a] - w->origin[a]);
+    o->scene_hi[a] = (float)(w->scene_hi[a] - w->origin[a]);
+    o->inv_size[a] = (float)(1.0 / w->tile_size[a]);
+  }
+  o->split[0] = (float)w->tile_size[0];
+  o->split[1] = (float)w->tile_size[1];
+  o->nx = w->nx;
+  o->ny = w->ny;
+  for (int q = 0; q < 4; ++q) o->slot[q] = q < n_slots ? w->slot[q] : 0;
+  o->n_slots = n_slots;
+  return SNK_OK;
+}
+
+int check_sampler(snk_ctx *ctx, const snk_sampler *s, SamplerParams *o) {
+  if (!s) return fail(ctx, SNK_ERR_INVALID_ARG, "sampler is NULL");
+  if (s->K_min < 1 || s->K_max < s->K_min || s->K_max > 4096 || s->K_ray < 1 || s->K_ray > 4096)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "need 1 <= K_min <= K_max <= 4096 and 1 <= K_ray <= 4096");
+  o->K_ray = s->K_ray;
+  o->K_min = s->K_min;
+  o->K_max = s->K_max;
+  o->render = s->render ? 1 : 0;
+  o->seed = s->seed;
+  o->iteration = s->iteration;
+  o->use_state_iteration = 0;
+  return SNK_OK;
+}
+
+size_t carve(size_t &off, size_t bytes) {
+  const size_t o = off;
+  off += (bytes + 255) / 256 * 256;
+  return o;
+}
+
+// Lay the workspace out for B rays and S samples; with base == nullptr only sizes it.
+size_t layout_ws(snk_ctx *ctx, char *base, int64_t B, int64_t S) {
+  size_t off = 0;
+  const int64_t nb = scan_blocks((int)B > 0 ? (int)B : 1);
+  RayBuffers rb{};
+  rb.ray_od = (float *)(base + carve(off, sizeof(float) * 6 * B));
+  rb.ray_ok = (uint8_t *)(base + carve(off, B));
+  rb.seg_slot = (uint8_t *)(base + carve(off, 3 * B));
+  rb.seg_t = (float *)(base + carve(off, sizeof(float) * 6 * B));
+  rb.seg_n = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 3 * B));
+  rb.seg_off = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 3 * B));
+  rb.cnt = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 5 * B));
+  rb.excl = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 5 * B));
+  rb.block_tot = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 5 * nb));
+  rb.smp_t = (float *)(base + carve(off, sizeof(float) * S));
+  rb.smp_dt = (float *)(base + carve(off, sizeof(float) * S));
+  rb.smp_xyz = (float *)(base + carve(off, sizeof(float) * 3 * S));
+  float *sr = (float *)(base + carve(off, sizeof(float) * 4 * S));
+  float *dsr = (float *)(base + carve(off, sizeof(float) * 4 * S));
+  if (base) {
+    ctx->rb = rb;
+    ctx->sigma_rgb = sr;
+    ctx->dsr = dsr;
+  }
+  return off;
+}
+
+int ensure_ws(snk_ctx *ctx, int64_t B, int64_t S) {
+  if (B <= ctx->cap_rays && S <= ctx->cap_samples && ctx->ws) return SNK_OK;
+  const int64_t nB = B > ctx->cap_rays ? B : ctx->cap_rays;
+  const int64_t nS = S > ctx->cap_samples ? S : ctx->cap_samples;
+  const size_t bytes = layout_ws(ctx, nullptr, nB, nS);
+  if (ctx->ws) {
+    SNK_CK(ctx, cudaDeviceSynchronize());
+    SNK_CK(ctx, cudaFree(ctx->ws));
+    ctx->ws = nullptr;
+  }
+  if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    ctx->cap_rays = ctx->cap_samples = 0;
+    return fail(ctx, SNK_ERR_OOM, "workspace of %zu bytes (%lld rays, %lld samples) could not be allocated", bytes,
+                (long long)nB, (long long)nS);
+  }
+  ctx->ws_bytes = bytes;
+  ctx->cap_rays = nB;
+  ctx->cap_samples = nS;
+  layout_ws(ctx, (char *)ctx->ws, nB, nS);
+  return SNK_OK;
+}
+
+int64_t max_samples_for(const snk_window *w, const snk_sampler *s, int64_t B) {
+  const int segs = 1 + (w->nx == 2 ? 1 : 0) + (w->ny == 2 ? 1 : 0);
+  return B * segs * (int64_t)s->K_max + (int64_t)kSlotAlign * kMaxSlots;
+}
+
+int prepare(snk_ctx *ctx, const snk_model *model, snk_layout *lay, ModelDev *md) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  const int rc = layout_of(model, lay, ctx->err, sizeof(ctx->err));
+  if (rc != SNK_OK) return rc;
+  *md = model_dev(model, *lay);
+  return SNK_OK;
+}
+
+int check_params(snk_ctx *ctx, const snk_model *model, const snk_params *p, bool train) {
+  if (!p || !p->params) return fail(ctx, SNK_ERR_INVALID_ARG, "params is NULL");
+  if (model->precision == SNK_MIXED && !p->params_lp)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "mixed precision needs the params_lp working copy");
+  if (train && (!p->grads || !p->adam_m || !p->adam_v || !p->adam_step))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "training needs grads, adam_m, adam_v and adam_step");
+  return SNK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *snk_version(void) { return "libsnk 0.1 (sm_103a)"; }
+
+int snk_abi_sizes(int64_t *sizes, int n) {
+  const int64_t all[8] = {(int64_t)sizeof(snk_camera), (int64_t)sizeof(snk_window), (int64_t)sizeof(snk_model),
+                          (int64_t)sizeof(snk_layout), (int64_t)sizeof(snk_sampler), (int64_t)sizeof(snk_adam),
+                          (int64_t)sizeof(snk_params), (int64_t)sizeof(snk_state)};
+  if (!sizes || n < 0) return 0;
+  const int k = n < 8 ? n : 8;
+  for (int i = 0; i < k; ++i) sizes[i] = all[i];
+  return k;
+}
+
+int snk_model_layout(const snk_model *model, snk_layout *out) {
+  char msg[256];
+  return layout_of(model, out, msg, sizeof(msg));
+}
+
+int snk_ctx_create(int device, snk_ctx **out) {
+  if (!out) return SNK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return SNK_ERR_CUDA;
+  }
+  snk_ctx *c = new snk_ctx();
+  c->device = device;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+    c->sm_count = sms;
+  if (cudaMalloc(&c->d_views, sizeof(DevView) * kMaxViews) != cudaSuccess ||
+      cudaMallocHost(&c->h_views, sizeof(DevView) * kMaxViews) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->d_views) cudaFree(c->d_views);
+    delete c;
+    return SNK_ERR_OOM;
+  }
+  *out = c;
+  return SNK_OK;
+}
+
+int snk_ctx_destroy(snk_ctx *ctx) {
+  if (!ctx) return SNK_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_views) cudaFree(ctx->d_views);
+  if (ctx->h_views) cudaFreeHost(ctx->h_views);
+  delete ctx;
+  return SNK_OK;
+}
+
+int snk_ctx_reserve(snk_ctx *ctx, int64_t max_rays, int64_t max_samples) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (max_rays < 1 || max_rays > (1 << 22) || max_samples < 0 || max_samples > 0xFFFFFF00ll)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "reserve: need 1 <= max_rays <= 2^22 and 0 <= max_samples < 2^32");
+  return ensure_ws(ctx, max_rays, max_samples);
+}
+
+const char *snk_last_error(const snk_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }
+
+int snk_set_views(snk_ctx *ctx, const snk_camera *cams, int n_views, const float *const *crops, snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (!cams || n_views < 1 || n_views > kMaxViews)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "need 1..%d cameras", kMaxViews);
+  SNK_CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));  // the staging buffer may still be in flight
+  for (int v = 0; v < n_views; ++v) {
+    const snk_camera &c = cams[v];
+    if (c.kind != SNK_CAM_AFFINE && c.kind != SNK_CAM_RPC3)
+      return fail(ctx, SNK_ERR_INVALID_ARG, "camera %d: unknown kind %d", v, c.kind);
+    if (c.crop_h < 0 || c.crop_w < 0 || c.crop_r0 < 0 || c.crop_c0 < 0 || c.crop_r0 + c.crop_h > 4096 ||
+        c.crop_c0 + c.crop_w > 4096)
+      return fail(ctx, SNK_ERR_INVALID_ARG, "camera %d: crop outside 0..4095", v);
+    if (c.kind == SNK_CAM_RPC3)
+      for (int q = 0; q < 3; ++q)
+        if (c.scale[q] == 0.0) return fail(ctx, SNK_ERR_INVALID_ARG, "camera %d: zero normalisation scale", v);
+    DevView &d = ctx->h_views[v];
+    memset(&d, 0, sizeof(d));
+    d.kind = c.kind;
+    d.width = c.width;
+    d.height = c.height;
+    d.crop_r0 = c.crop_r0;
+    d.crop_c0 = c.crop_c0;
+    d.crop_h = c.crop_h;
+    d.crop_w = c.crop_w;
+    memcpy(d.a, c.a, sizeof(d.a));
+    memcpy(d.b, c.b, sizeof(d.b));
+    memcpy(d.off, c.off, sizeof(d.off));
+    memcpy(d.scale, c.scale, sizeof(d.scale));
+    memcpy(d.coef, c.coef, sizeof(d.coef));
+    d.crop = crops ? crops[v] : nullptr;
+  }
+  SNK_CK(ctx, cudaMemcpyAsync(ctx->d_views, ctx->h_views, sizeof(DevView) * n_views, cudaMemcpyHostToDevice,
+                              (cudaStream_t)stream));
+  SNK_CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  ctx->n_views = n_views;
+  return SNK_OK;
+}
+
+int snk_sample_segments(snk_ctx *ctx, const snk_window *win, const uint32_t *pix, int B, const snk_sampler *sampler,
+                        float *ray_od, uint8_t *ray_ok, uint8_t *seg_slot, float *seg_t, uint32_t *seg_n,
+                        uint32_t *seg_off, float *smp_t, float *smp_dt, float *smp_xyz, int64_t cap, snk_state *state,
+                        snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (B < 0 || B > (1 << 22)) return fail(ctx, SNK_ERR_INVALID_ARG, "B must be in 0..2^22");
+  if (!win) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
+  WinParams wp;
+  int rc = check_window(ctx, win, win->nx * win->ny, &wp);
+  if (rc) return rc;
+  SamplerParams sp;
+  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
+  if (B > 0 && (!pix || !ray_od || !ray_ok || !seg_slot || !seg_t || !seg_n || !seg_off || !smp_t || !smp_dt ||
+                !smp_xyz || !state))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer");
+  if ((rc = ensure_ws(ctx, B > 0 ? B : 1, ctx->cap_samples))) return rc;
+  RayBuffers rb = ctx->rb;
+  rb.ray_od = ray_od;
+  rb.ray_ok = ray_ok;
+  rb.seg_slot = seg_slot;
+  rb.seg_t = seg_t;
+  rb.seg_n = seg_n;
+  rb.seg_off = seg_off;
+  rb.smp_t = smp_t;
+  rb.smp_dt = smp_dt;
+  rb.smp_xyz = smp_xyz;
+  SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, rb, cap, state,
+                                     (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_encode(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *smp_xyz,
+               const snk_state *state, int64_t S, float *feat, uint32_t *idx_out, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  if (!p || !p->params || !smp_xyz || !state || !feat || S < 0)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative S");
+  FieldArgs fa{};
+  fa.m = md;
+  fa.params = p->params;
+  fa.xyz = smp_xyz;
+  fa.feat_out = feat;
+  fa.idx_out = idx_out;
+  fa.state = state;
+  fa.S = S;
+  fa.slot_only = -1;
+  fa.mode = kEncodeOnly;
+  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_encode_backward(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *smp_xyz,
+                        const snk_state *state, int64_t S, const float *dfeat, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  if (!p || !p->grads || !smp_xyz || !state || !dfeat || S < 0)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative S");
+  FieldArgs fa{};
+  fa.m = md;
+  fa.grads = p->grads;
+  fa.xyz = smp_xyz;
+  fa.feat_in = dfeat;
+  fa.state = state;
+  fa.S = S;
+  fa.slot_only = -1;
+  SNK_CK(ctx, launch_encode_scatter(fa, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_mlp(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *feat, const snk_state *state,
+            int64_t S, float *out, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  if (!p || !p->params || !feat || !state || !out || S < 0)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative S");
+  FieldArgs fa{};
+  fa.m = md;
+  fa.params = p->params;
+  fa.feat_in = feat;
+  fa.sigma_rgb = out;
+  fa.state = state;
+  fa.S = S;
+  fa.slot_only = -1;
+  fa.mode = kForward;
+  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_mlp_backward(snk_ctx *ctx, const snk_model *model, const snk_params *p, const float *feat,
+                     const snk_state *state, int64_t S, const float *dout, float *dfeat, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  if (!p || !p->params || !p->grads || !feat || !state || !dout || !dfeat || S < 0)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative S");
+  FieldArgs fa{};
+  fa.m = md;
+  fa.params = p->params;
+  fa.grads = p->grads;
+  fa.feat_in = feat;
+  fa.dsr = dout;
+  fa.dfeat_out = dfeat;
+  fa.state = state;
+  fa.S = S;
+  fa.slot_only = -1;
+  fa.mode = kBackward;
+  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_composite(snk_ctx *ctx, const float *sigma_rgb, const float *smp_t, const float *smp_dt,
+                  const uint32_t *seg_n, const uint32_t *seg_off, int B, float *out, float *t_final,
+                  snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (B < 0 || (B > 0 && (!sigma_rgb || !smp_t || !smp_dt || !seg_n || !seg_off || !out)))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative B");
+  CompositeArgs ca{};
+  ca.sigma_rgb = sigma_rgb;
+  ca.smp_t = smp_t;
+  ca.smp_dt = smp_dt;
+  ca.seg_n = seg_n;
+  ca.seg_off = seg_off;
+  ca.B = B;
+  ca.out = out;
+  ca.t_final = t_final;
+  SNK_CK(ctx, launch_composite(ca, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_composite_backward(snk_ctx *ctx, const float *sigma_rgb, const float *smp_t, const float *smp_dt,
+                           const uint32_t *seg_n, const uint32_t *seg_off, int B, const float *g_rgb,
+                           float *d_sigma_rgb, snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (B < 0 || (B > 0 && (!sigma_rgb || !smp_t || !smp_dt || !seg_n || !seg_off || !g_rgb || !d_sigma_rgb)))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative B");
+  CompositeArgs ca{};
+  ca.sigma_rgb = sigma_rgb;
+  ca.smp_t = smp_t;
+  ca.smp_dt = smp_dt;
+  ca.seg_n = seg_n;
+  ca.seg_off = seg_off;
+  ca.B = B;
+  ca.g_rgb = g_rgb;
+  ca.dsr = d_sigma_rgb;
+  SNK_CK(ctx, launch_composite(ca, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, const snk_params *p,
+                     const snk_state *state, int mode, cudaStream_t st) {
+  FieldArgs fa{};
+  fa.m = md;
+  fa.params = p->params;
+  fa.params_lp = p->params_lp;
+  fa.grads = p->grads;
+  fa.xyz = ctx->rb.smp_xyz;
+  fa.sigma_rgb = ctx->sigma_rgb;
+  fa.dsr = ctx->dsr;
+  fa.state = state;
+  fa.S = ctx->cap_samples;
+  fa.mode = mode;
+  if (model->precision == SNK_MIXED) {
+    fa.slot_only = -1;
+    SNK_CK(ctx, launch_field_tc(fa, ctx->sm_count, st));
+    return SNK_OK;
+  }
+  // binary32 path: one launch chain per tile (slot), as a per-tile trainer issues them
+  for (int k = 0; k < model->n_slots; ++k) {
+    fa.slot_only = k;
+    SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, st));
+  }
+  return SNK_OK;
+}
+
+int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
+                   const snk_sampler *sampler, const snk_adam *adam, const snk_params *p, snk_state *state,
+                   float *out, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  WinParams wp;
+  if ((rc = check_window(ctx, win, model->n_slots, &wp))) return rc;
+  SamplerParams sp;
+  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  sp.use_state_iteration = 1;
+  sp.render = 0;
+  if ((rc = check_params(ctx, model, p, true))) return rc;
+  if (!adam) return fail(ctx, SNK_ERR_INVALID_ARG, "adam is NULL");
+  if (!state || !pix || B < 1 || B > (1 << 22)) return fail(ctx, SNK_ERR_INVALID_ARG, "need state, pix, 1 <= B <= 2^22");
+  if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
+  if ((rc = ensure_ws(ctx, B, max_samples_for(win, sampler, B)))) return rc;
+  const cudaStream_t st = (cudaStream_t)stream;
+  SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, ctx->rb, ctx->cap_samples, state, st));
+  if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  CompositeArgs ca{};
+  ca.sigma_rgb = ctx->sigma_rgb;
+  ca.smp_t = ctx->rb.smp_t;
+  ca.smp_dt = ctx->rb.smp_dt;
+  ca.seg_n = ctx->rb.seg_n;
+  ca.seg_off = ctx->rb.seg_off;
+  ca.B = B;
+  ca.out = out;
+  ca.pix = pix;
+  ca.views = ctx->d_views;
+  ca.dsr = ctx->dsr;
+  ca.state = state;
+  ca.train = 1;
+  SNK_CK(ctx, launch_composite(ca, st));
+  if ((rc = run_field(ctx, model, md, p, state, kBackward, st))) return rc;
+  AdamArgs aa{};
+  aa.params = p->params;
+  aa.params_lp = p->params_lp;
+  aa.grads = p->grads;
+  aa.m = p->adam_m;
+  aa.v = p->adam_v;
+  aa.steps = p->adam_step;
+  aa.n = lay.n_params;
+  aa.n_groups = lay.n_optimisers;
+  for (int k = 0; k < model->n_slots; ++k) {
+    aa.start[k] = k * lay.tile_params;
+    aa.end[k] = aa.start[k] + lay.tile_params;
+    aa.mlp_start[k] = aa.start[k] + lay.grid_params;
+  }
+  for (int c = 0; c < lay.n_colour_blocks; ++c) {
+    const int k = model->n_slots + c;
+    aa.start[k] = md.colour_base + c * lay.colour_params;
+    aa.end[k] = aa.start[k] + lay.colour_params;
+    aa.mlp_start[k] = aa.start[k];
+  }
+  aa.lr = adam->lr;
+  aa.beta1 = adam->beta1;
+  aa.beta2 = adam->beta2;
+  aa.eps = adam->eps;
+  aa.l2 = adam->l2_mlp;
+  aa.state = state;
+  aa.mixed = model->precision == SNK_MIXED;
+  SNK_CK(ctx, launch_adam(aa, ctx->sm_count, st));
+  return SNK_OK;
+}
+
+int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
+               const snk_sampler *sampler, const snk_params *p, snk_state *state, float *out, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  WinParams wp;
+  if ((rc = check_window(ctx, win, model->n_slots, &wp))) return rc;
+  SamplerParams sp;
+  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  sp.render = 1;
+  if ((rc = check_params(ctx, model, p, false))) return rc;
+  if (!state || !pix || !out || B < 1 || B > (1 << 22))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "need state, pix, out and 1 <= B <= 2^22");
+  if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
+  if ((rc = ensure_ws(ctx, B, max_samples_for(win, sampler, B)))) return rc;
+  const cudaStream_t st = (cudaStream_t)stream;
+  SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state, st));
+  if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  CompositeArgs ca{};
+  ca.sigma_rgb = ctx->sigma_rgb;
+  ca.smp_t = ctx->rb.smp_t;
+  ca.smp_dt = ctx->rb.smp_dt;
+  ca.seg_n = ctx->rb.seg_n;
+  ca.seg_off = ctx->rb.seg_off;
+  ca.B = B;
+  ca.out = out;
+  ca.state = state;
+  SNK_CK(ctx, launch_composite(ca, st));
+  return SNK_OK;
+}
+
+int snk_sync_status(snk_ctx *ctx, const snk_state *state, snk_stream_t stream) {
+  if (!ctx || !state) return SNK_ERR_INVALID_ARG;
+  SNK_CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  uint32_t status = 0;
+  SNK_CK(ctx, cudaMemcpy(&status, &state->status, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status & kStatusCheck) return fail(ctx, SNK_ERR_DEVICE_CHECK, "a device-side check failed (status %u)", status);
+  if (status & kStatusTimeout) return fail(ctx, SNK_ERR_TIMEOUT, "a bounded device wait gave up (status %u)", status);
+  if (status & kStatusOverflow) return fail(ctx, SNK_ERR_OVERFLOW, "a step was skipped on non-finite gradients");
+  return SNK_OK;
+}
+
+}  // extern "C"

@@ -55,6 +55,8 @@ struct FieldArgs {
 };
 cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st);
 cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st);
+// Scatter-add feat_in (read as dfeat [S][L*F]) into the table gradients.
+cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st);
 
 struct CompositeArgs {
   const float *sigma_rgb;

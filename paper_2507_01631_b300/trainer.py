@@ -1,0 +1,80 @@
+"""Tensor plumbing around libsnk: allocates the trainable state and the per-step
+device state as torch tensors and calls snk_train_step / snk_render.  No step
+of the method is computed here."""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import snk
+
+STATE_FIELDS = {"loss": (0, "f"), "loss_scale": (1, "f"), "n_accepted": (2, "u"), "n_samples": (3, "u"),
+                "status": (4, "u"), "good_steps": (5, "i"), "iteration": (6, "u")}
+
+
+def model_from_workload(w, precision=None, hidden=64):
+    prec = precision if precision is not None else (snk.SNK_MIXED if w.mixed else snk.SNK_FP32)
+    return snk.model_struct(w.L, w.F, w.log2_T, w.n_min, w.n_max, w.geo_out, w.colour, w.shared_colour,
+                            w.n_slots, prec, hidden)
+
+
+def low_precision_copy(params, lay, model):
+    """FP16 (tables) / BF16 (MLP weights) working copy of binary32 parameters,
+    returned as int16 bit patterns in the flat layout."""
+    out = torch.empty(params.numel(), dtype=torch.int16, device=params.device)
+    n_slots = model.n_slots
+    for k in range(n_slots):
+        a = k * lay.tile_params
+        g = a + lay.grid_params
+        b = a + lay.tile_params
+        out[a:g] = params[a:g].to(torch.float16).view(torch.int16)
+        out[g:b] = params[g:b].to(torch.bfloat16).view(torch.int16)
+    c0 = n_slots * lay.tile_params
+    out[c0:] = params[c0:].to(torch.bfloat16).view(torch.int16)
+    return out
+
+
+class Trainer:
+    """One model (1 tile or a 2x2 window) with its Adam state on a CUDA device."""
+
+    def __init__(self, ctx, model, window, sampler, init_params, adam=None, loss_scale=None, device="cuda"):
+        self.ctx = ctx
+        self.model = model
+        self.window = window
+        self.sampler = sampler
+        self.adam = adam or snk.adam_struct()
+        self.lay = snk.layout(model)
+        n = self.lay.n_params
+        p = torch.as_tensor(np.asarray(init_params, np.float32)).to(device)
+        assert p.numel() == n, (p.numel(), n)
+        self.params = p.contiguous()
+        self.mixed = model.precision == snk.SNK_MIXED
+        self.params_lp = low_precision_copy(self.params, self.lay, model) if self.mixed else None
+        self.grads = torch.zeros(n, dtype=torch.float32, device=device)
+        self.m = torch.zeros(n, dtype=torch.float32, device=device)
+        self.v = torch.zeros(n, dtype=torch.float32, device=device)
+        self.steps = torch.zeros(self.lay.n_optimisers, dtype=torch.int32, device=device)
+        self.state = torch.zeros(snk.STATE_WORDS, dtype=torch.int32, device=device)
+        scale = loss_scale if loss_scale is not None else (65536.0 if self.mixed else 1.0)
+        self.state.view(torch.float32)[1] = scale
+        self.p_struct = snk.SnkParams(snk.ptr(self.params), snk.ptr(self.params_lp), snk.ptr(self.grads),
+                                      snk.ptr(self.m), snk.ptr(self.v), snk.ptr(self.steps))
+
+    def train_step(self, pix, out=None, stream=None):
+        self.ctx.call("snk_train_step", ctypes.byref(self.model), ctypes.byref(self.window), snk.ptr(pix),
+                      int(pix.numel()), ctypes.byref(self.sampler), ctypes.byref(self.adam),
+                      ctypes.byref(self.p_struct), snk.ptr(self.state), snk.ptr(out), snk.stream_handle(stream))
+
+    def render(self, pix, out, stream=None):
+        self.ctx.call("snk_render", ctypes.byref(self.model), ctypes.byref(self.window), snk.ptr(pix),
+                      int(pix.numel()), ctypes.byref(self.sampler), ctypes.byref(self.p_struct),
+                      snk.ptr(self.state), snk.ptr(out), snk.stream_handle(stream))
+
+    def read_state(self):
+        s = self.state.cpu().numpy()
+        out = {}
+        for k, (i, t) in STATE_FIELDS.items():
+            out[k] = float(s[i:i + 1].view(np.float32)[0]) if t == "f" else int(s[i:i + 1].view(np.uint32)[0])
+        out["slot_base"] = s[7:12].view(np.uint32).tolist()
+        out["slot_count"] = s[12:16].view(np.uint32).tolist()
+        return out

@@ -1,0 +1,78 @@
+"""The C-ABI library loads, exports every function include/snk.h declares, its
+structs match the binding's mirrors, and its host-only layout agrees with the
+oracle's (CPU only: no compute call needs a GPU here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2507_01631_b300 import build, snk
+from oracle import hashgrid
+from synth import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return snk.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "snk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(snk_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(snk.SIGNATURES), set(names) ^ set(snk.SIGNATURES)
+
+
+def test_struct_sizes_match_the_binding(lib):
+    sizes = (ctypes.c_int64 * 8)()
+    assert lib.snk_abi_sizes(sizes, 8) == 8
+    for s, cls in zip(sizes, snk.STRUCTS):
+        assert s == ctypes.sizeof(cls), cls.__name__
+    assert lib.snk_version().startswith(b"libsnk")
+
+
+@pytest.mark.parametrize("name", list(W.WORKLOADS))
+def test_model_layout_matches_the_oracle(lib, name):
+    w = W.get(name)
+    from paper_2507_01631_b300.trainer import model_from_workload
+    lay = snk.layout(model_from_workload(w))
+    ref = hashgrid.layout(w.L, w.F, w.log2_T, w.n_min, w.n_max)
+    assert list(lay.res[:w.L]) == ref.res.tolist()
+    assert list(lay.dense[:w.L]) == ref.dense.astype(int).tolist()
+    assert list(lay.level_offset[:w.L]) == ref.offset.tolist()
+    assert list(lay.level_size[:w.L]) == ref.size.tolist()
+    assert lay.n_entries == ref.n_entries
+    from oracle.step import ModelConfig
+    cfg = ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, geo_out=w.geo_out,
+                      colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots)
+    assert lay.tile_params == cfg.tile_params()
+    assert lay.n_params == cfg.n_params()
+    assert lay.n_optimisers == cfg.n_optimisers()
+
+
+@pytest.mark.parametrize("field,value", [("F", 3), ("L", 5), ("hidden", 32), ("geo_out", 8), ("n_slots", 5),
+                                         ("log2_T", 30), ("precision", 7), ("n_min", 1)])
+def test_invalid_models_are_rejected(lib, field, value):
+    m = snk.model_struct(8, 2, 14, 16, 256, 4, 0, 1, 1, snk.SNK_FP32)
+    setattr(m, field, value)
+    out = snk.SnkLayout()
+    assert lib.snk_model_layout(ctypes.byref(m), ctypes.byref(out)) == snk.SNK_ERR_INVALID_ARG
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    assert lib.snk_model_layout(None, None) == snk.SNK_ERR_INVALID_ARG
+    assert lib.snk_ctx_reserve(None, 1, 1) == snk.SNK_ERR_INVALID_ARG
+    assert lib.snk_ctx_destroy(None) == snk.SNK_OK
+    assert lib.snk_sync_status(None, None, None) == snk.SNK_ERR_INVALID_ARG
