@@ -168,8 +168,9 @@ class Samples:
     xyz: np.ndarray     # (S, 3) float32 tile-local coordinates in [0, 1]
 
 
-def stratified(o, d, seg, wf, seed, iteration, render=False):
-    """Sample positions of every segment (see module docstring).
+def stratified(o, d, seg, wf, seed, iteration, render=False, ray_ids=None):
+    """Sample positions of every segment (see module docstring).  `ray_ids`
+    gives each ray's index in its batch (the jitter counter); default 0..B-1.
     Sample k of a segment [t0, t1] with K bins of width w = (t1 - t0) / K sits
     at t = t0 + (k + u) * w, u = jitter of its index along the ray (0.5 when
     rendering); world point p = o + t d; tile-local l = clamp((p - tile_lo) *
@@ -186,7 +187,8 @@ def stratified(o, d, seg, wf, seed, iteration, render=False):
             if render:
                 u = np.full(k_n, F32(0.5), F32)
             else:
-                u = philox.jitter(seed, iteration, i, j0 + k).astype(F32)
+                rid = i if ray_ids is None else int(ray_ids[i])
+                u = philox.jitter(seed, iteration, rid, j0 + k).astype(F32)
             t = (a + ((k.astype(F32) + u).astype(F32) * w).astype(F32)).astype(F32)
             sl = int(seg.slot[i, s])
             tile = wf.slot.index(sl)

@@ -125,11 +125,11 @@ class StepResult:
     extra: dict = field(default_factory=dict)
 
 
-def sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode):
+def sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids=None):
     o, d = camera.rays(cameras, pix, win.origin, win.origin[2], win.origin[2] + win.tile_size[2])
     wf = sampler.window_f32(win)
     seg = sampler.segments(o, d, wf, cfg.K_ray, cfg.K_min, cfg.K_max)
-    smp = sampler.stratified(o, d, seg, wf, seed, iteration, render=render_mode)
+    smp = sampler.stratified(o, d, seg, wf, seed, iteration, render=render_mode, ray_ids=ray_ids)
     return o, d, seg, smp
 
 
@@ -199,9 +199,10 @@ def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, s
     return res
 
 
-def render_rays(cfg, flat, cameras, win, pix):
-    """Forward only, u = 0.5: per-ray rgb, depth, opacity."""
-    o, d, seg, smp = sample_rays(cfg, cameras, win, pix, 0, 0, True)
+def render_rays(cfg, flat, cameras, win, pix, seed=0, iteration=0, render_mode=True, ray_ids=None):
+    """Forward only: per-ray rgb, depth, opacity (bin-centre samples unless
+    render_mode is False, then the training jitter of the given ray ids)."""
+    o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids)
     sigma, rgb_s, _ = field_forward(cfg, flat, smp)
     rgb, depth, opac, tfin, _ = render.composite(sigma, rgb_s, smp.t.astype(np.float64),
                                                  smp.dt.astype(np.float64), seg.ray_off)

@@ -1,0 +1,98 @@
+"""Helpers shared by the GPU parity tests: build the same seeded case for the
+CUDA library and for the FP64 oracle, and map the library's slot-major sample
+arrays onto the oracle's ray-major order."""
+import dataclasses
+
+import numpy as np
+
+import synth
+from synth import workloads as W
+from oracle import step as OS, targets as OT
+
+RGB_REL_FP32 = 1e-5      # rendered RGB and depth, binary32 path
+GRAD_REL_FP32 = 1e-4     # gradients (norm-wise per tensor), binary32 path
+RGB_REL_MIXED = 2e-3
+GRAD_REL_MIXED = 5e-3
+
+
+def close(a, b, rel):
+    """Elementwise |a - b| <= rel |b| + rel max|b| (floor for near-zero entries)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    floor = rel * (np.max(np.abs(b)) if b.size else 0.0)
+    err = np.abs(a - b) - (rel * np.abs(b) + floor)
+    return bool(np.all(err <= 0)), float(np.max(np.abs(a - b)) if a.size else 0.0)
+
+
+def normwise(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def small_crops(cams, size, seed=0):
+    """Shrink every view's crop to a size x size square near the image centre
+    (keeps oracle target rendering cheap for the full-size cameras)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in cams:
+        h = min(size, c.height)
+        w = min(size, c.width)
+        r0 = int(rng.integers(max(0, c.height // 2 - 2 * h), max(1, c.height // 2 + h)))
+        c0 = int(rng.integers(max(0, c.width // 2 - 2 * w), max(1, c.width // 2 + w)))
+        r0 = min(r0, c.height - h)
+        c0 = min(c0, c.width - w)
+        out.append(dataclasses.replace(c, crop=(r0, c0, h, w)))
+    return out
+
+
+def model_config(w, hidden=64):
+    return OS.ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, hidden=hidden,
+                          geo_out=w.geo_out, colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots,
+                          K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max)
+
+
+@dataclasses.dataclass
+class Case:
+    w: object
+    cams: list
+    targets: list
+    cfg: object
+    params: np.ndarray
+    pix: np.ndarray
+
+
+def make_case(name, n_rays=None, crop=None, seed=0, table_scale=None, with_targets=True, **over):
+    w = W.get(name, **over) if over else W.get(name)
+    if n_rays is not None:
+        w = dataclasses.replace(w, n_rays=n_rays)
+    cams = W.cameras(w)
+    if crop is not None:
+        cams = small_crops(cams, crop, seed)
+    targets = OT.render_targets(W.scene(w), cams) if with_targets else None
+    cfg = model_config(w)
+    lay = cfg.grid()
+    params = W.init_params(lay.n_params, cfg.geo_shapes(), cfg.col_shapes(), cfg.n_slots, cfg.n_colour_blocks(),
+                           seed)
+    if table_scale is not None:
+        rng = np.random.default_rng(seed + 5)
+        for a, b, mlp_a in OS.group_ranges(cfg)[:cfg.n_slots]:
+            params[a:mlp_a] = rng.uniform(-table_scale, table_scale, mlp_a - a).astype(np.float32)
+    # with shrunken crops every pixel is drawn inside its view's crop
+    pix = synth.random_pixels(seed + 3, w.n_rays, cams) if crop is not None else W.batch(w, cams, seed + 3)
+    return Case(w, cams, targets, cfg, params, pix)
+
+
+def gpu_to_ray_major(seg_n, seg_off, ray_off_oracle):
+    """Index into the slot-major arrays for every oracle (ray-major) sample."""
+    B = seg_n.shape[0]
+    idx = np.zeros(int(ray_off_oracle[-1]), np.int64)
+    for r in range(B):
+        p = int(ray_off_oracle[r])
+        for s in range(3):
+            n = int(seg_n[r, s])
+            if n:
+                idx[p:p + n] = int(seg_off[r, s]) + np.arange(n)
+                p += n
+    return idx
