@@ -1,0 +1,378 @@
+"""Benchmark of the Snake-NeRF training step on B300: train samples/s for the
+full step (rays, segments, samples, encoding, MLPs, rendering, loss,
+backward, Adam) on synthetic satellite-like data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision fp32|mixed|both] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank trains an
+independent replica on its own GPU ("replicas only": the step has no
+exchange); value = samples of all ranks / max elapsed over ranks.
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same
+workload (the reference arm; rank 0 only).
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import workloads as W  # noqa: E402
+import synth  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}
+METRIC = "train samples/s (fwd+bwd+Adam), FP32 per-tile vs mixed 2x2-batched, equal PSNR"
+N_BATCHES = 4  # distinct ray batches cycled through the timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="tile512_full")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-rays", type=int, default=256, help="rays per oracle sample (CPU baseline)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage-timing", type=int, default=1)
+    return ap.parse_args()
+
+
+def peaks():
+    if os.path.exists(PEAKS_FILE):
+        d = json.load(open(PEAKS_FILE))
+        d["source"] = "measured"
+        return d
+    d = dict(FALLBACK_PEAKS)
+    d["source"] = "fallback"
+    return d
+
+
+# ---- per-sample algorithmic work (see the design notes) ------------------------
+def mlp_flops_per_sample(w):
+    IN, H, G = w.L * w.F, 64, w.geo_out
+    mac = IN * H + H * H + H * G + ((G * H + H * H + H * 3) if w.colour else 0)
+    return 2 * mac
+
+
+def field_backward_work(w, precision):
+    """Algorithmic FLOPs and bytes per sample of the fused field backward:
+    recomputed MLP forward + input gradients + weight gradients (3 x the
+    forward MACs), the 8-corner gather of L levels x F features and the
+    8-corner scatter-add (read + write of F binary32 per corner)."""
+    fl = 3 * mlp_flops_per_sample(w)
+    tbytes = 2 if precision == "mixed" else 4
+    gather = w.L * 8 * w.F * tbytes
+    scatter = w.L * 8 * w.F * 4 * 2
+    stream = 12 + 16  # xyz in, (dsigma, drgb) in
+    return fl, gather + scatter + stream
+
+
+def field_forward_work(w, precision):
+    tbytes = 2 if precision == "mixed" else 4
+    return mlp_flops_per_sample(w), w.L * 8 * w.F * tbytes + 12 + 16
+
+
+# ---- clocks -------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- reference arm / CPU baseline: the FP64 oracle ------------------------------
+def oracle_sample(w, cams, targets, params, seed, n_rays):
+    """Time one oracle training step on n_rays rays of the workload; returns
+    (samples, seconds)."""
+    from oracle import step as OS
+    cfg = OS.ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, hidden=64,
+                         geo_out=w.geo_out, colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots,
+                         K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max)
+    pix = W.batch(w, cams, 1000 + seed, n_rays=n_rays)
+    flat = params.astype(np.float64)
+    n = len(flat)
+    t0 = time.perf_counter()
+    res = OS.train_step(cfg, flat, np.zeros(n), np.zeros(n), [0] * cfg.n_optimisers(), cams, w.window(), pix,
+                        targets, seed, 0)
+    dt = time.perf_counter() - t0
+    return int(res.seg.ray_off[-1]), dt
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 1) for d in threadpool_info()]
+        return max(n) if n else 1
+    except Exception:
+        return 1
+
+
+def make_inputs(w):
+    cams = W.cameras(w)
+    targets = synth.smooth_images(w.seed + 17, w.n_views, w.px, w.px)
+    from oracle import hashgrid  # sizes only
+    lay = hashgrid.layout(w.L, w.F, w.log2_T, w.n_min, w.n_max)
+    geo = [(64, w.L * w.F), (64, 64), (w.geo_out, 64)]
+    col = [(64, w.geo_out), (64, 64), (3, 64)] if w.colour else []
+    n_col = (1 if w.shared_colour else w.n_slots) if w.colour else 0
+    params = W.init_params(lay.n_params, geo, col, w.n_slots, n_col, w.seed)
+    return cams, targets, params
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cams, targets, params = make_inputs(w)
+    tot_s = tot_t = 0.0
+    for i in range(args.warmup):
+        oracle_sample(w, cams, targets, params, i, min(32, args.cpu_rays))
+    for i in range(args.steps):
+        s, t = oracle_sample(w, cams, targets, params, 100 + i, args.cpu_rays)
+        tot_s += s
+        tot_t += t
+    v = tot_s / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "rays_per_step": args.cpu_rays, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "%d oracle steps of %d rays of %s" % (args.steps, args.cpu_rays, w.name)},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm ------------------------------------------------------------------------
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+    from paper_2507_01631_b300 import snk, build as B
+    from paper_2507_01631_b300.trainer import Trainer, model_from_workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    precision = snk.SNK_MIXED if args.precision == "mixed" else snk.SNK_FP32
+    cams, targets, params = make_inputs(w)
+    ctx = snk.Context(local)
+    crops = [torch.from_numpy(t).cuda() for t in targets]
+    ctx.set_views(cams, crops)
+    model = model_from_workload(w, precision)
+    sampler = snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, 1234 + rank, 0)
+    tr = Trainer(ctx, model, snk.window_struct(w.window()), sampler, params)
+    batches_h = [W.batch(w, cams, 50 + i + 1000 * rank).view(np.int32) for i in range(N_BATCHES)]
+    batches = [torch.from_numpy(b).cuda() for b in batches_h]
+    nseg = 1 + (w.nx == 2) + (w.ny == 2)
+    ctx.reserve(w.n_rays, w.n_rays * nseg * w.K_max + 512)
+    stream = torch.cuda.current_stream()
+
+    # warm-up
+    for i in range(args.warmup):
+        tr.train_step(batches[i % N_BATCHES], stream=stream)
+    rc = ctx.sync_status(tr.state)
+    if rc not in (snk.SNK_OK, snk.SNK_ERR_OVERFLOW):
+        raise RuntimeError("warm-up failed with status %d: %s" % (rc, ctx.lib.snk_last_error(ctx.h)))
+
+    # timed region (device-resident inputs)
+    samples = []
+    clock = ClockSampler(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if args.stage_timing:
+        ctx.stage_timing(True)
+    launches0 = ctx.lib.snk_launch_count()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clock.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    n_state = []
+    for i in range(args.steps):
+        tr.train_step(batches[i % N_BATCHES], stream=stream)
+        n_state.append(tr.state[3:4].clone())  # n_samples of this step (device copy, no sync)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clock.stop()
+    launches = ctx.lib.snk_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    stages = ctx.stage_times() if args.stage_timing else {}
+    if args.stage_timing:
+        ctx.stage_timing(False)
+    n_samples = int(sum(int(x.view(torch.int32).item()) & 0xFFFFFFFF for x in n_state))
+    st = tr.read_state()
+    rc = ctx.sync_status(tr.state)
+
+    # end to end through host buffers: pinned pixels in, loss + counts out
+    pin_in = [torch.from_numpy(b).pin_memory() for b in batches_h]
+    pix_dev = torch.empty_like(batches[0])
+    state_host = torch.empty(snk.STATE_WORDS, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_samples = 0
+    for i in range(args.steps):
+        pix_dev.copy_(pin_in[i % N_BATCHES], non_blocking=True)
+        tr.train_step(pix_dev, stream=stream)
+        state_host.copy_(tr.state, non_blocking=True)
+        stream.synchronize()
+        e2e_samples += int(state_host[3].item()) & 0xFFFFFFFF
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    t_max = ms
+    tot_samples = n_samples
+    e2e_tot = e2e_samples
+    e2e_max = e2e_ms
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(t[0]), float(t[1])
+        c = torch.tensor([n_samples, e2e_samples], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        tot_samples, e2e_tot = float(c[0]), float(c[1])
+    value = tot_samples / (t_max / 1000.0)
+    e2e_value = e2e_tot / (e2e_max / 1000.0)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant stage
+    pk = peaks()
+    roof = None
+    if stages:
+        name, (sms, calls) = max(stages.items(), key=lambda kv: kv[1][0])
+        per_launch_s = (sms / max(calls, 1)) / 1000.0
+        per_step_samples = n_samples / max(args.steps, 1)
+        if name == "field_backward":
+            fl, by = field_backward_work(w, args.precision)
+        elif name == "field_forward":
+            fl, by = field_forward_work(w, args.precision)
+        else:
+            fl, by = 0, 0
+        if args.precision == "fp32" and fl:
+            sm_clk = (clk.get("sm_mhz") or pk.get("sm_max_mhz", 2032.0))
+            peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+            achieved = fl * per_step_samples / per_launch_s / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived)" % pk.get("sm_max_mhz", 2032.0),
+                    "sm_mhz_median": sm_clk}
+        elif fl:
+            achieved = by * per_step_samples / per_launch_s / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                    "peak_source": "%s hbm_gbs" % pk["source"]}
+        roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        from synth import workloads as W2  # noqa: F401
+        tot_s = tot_t = 0.0
+        for i in range(2):
+            s, t = oracle_sample(w, cams, targets, params, 200 + i, args.cpu_rays)
+            tot_s += s
+            tot_t += t
+        cpu = {"value": tot_s / tot_t, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": "2 oracle steps of %d rays of %s (%d samples), FP64 numpy" % (args.cpu_rays, w.name,
+                                                                                     int(tot_s))}
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
+        "config": {"workload": w.name, "precision": args.precision, "rays_per_step": w.n_rays,
+                   "samples_per_step": n_samples / args.steps, "tiles": w.n_slots,
+                   "grid": "L%d F%d T2^%d N%d-%d" % (w.L, w.F, w.log2_T, w.n_min, w.n_max),
+                   "views": "%d x %dpx %s" % (w.n_views, w.px, "rpc3" if w.cam_kind else "affine"),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set per step > L2 (sample buffers %.2f GB)" % (n_samples / args.steps * 52 / 1e9)},
+        "rays_per_s": st["n_accepted"] * args.steps / (ms / 1000.0) * world,
+        "final_loss": st["loss"], "status": rc,
+        "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(batches_h[0].nbytes),
+                "d2h_bytes_per_step": int(snk.STATE_WORDS * 4)},
+        "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    w = W.get(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -273,6 +273,19 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
                const snk_sampler *sampler, const snk_params *p, snk_state *state, float *out,
                snk_stream_t stream);
 
+/* ---- diagnostics -------------------------------------------------------- */
+
+/* Host only: number of kernels libsnk has launched in this process. */
+int64_t snk_launch_count(void);
+/* enable != 0: snk_train_step and snk_render record CUDA events on their
+ * stream around each stage (0 rays/segments/samples, 1 field forward,
+ * 2 rendering + loss + rendering backward, 3 field backward, 4 Adam).
+ * Enabling (again) clears what was recorded. */
+int snk_stage_timing(snk_ctx *ctx, int enable);
+/* Synchronise and return, per stage, the summed milliseconds and the number
+ * of recorded calls since timing was enabled (ms, calls: n entries, n <= 5). */
+int snk_stage_times(snk_ctx *ctx, double *ms, int64_t *calls, int n);
+
 /* Wait for `stream` and report device-side status bits of `state` as a
  * status code (SNK_ERR_DEVICE_CHECK, SNK_ERR_TIMEOUT, SNK_ERR_OVERFLOW). */
 int snk_sync_status(snk_ctx *ctx, const snk_state *state, snk_stream_t stream);

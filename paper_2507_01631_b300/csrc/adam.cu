@@ -78,6 +78,7 @@ cudaError_t launch_adam(const AdamArgs &a, int sm_count, cudaStream_t st) {
   if (a.mixed) k_check_finite<<<grid, 256, 0, st>>>(a.grads, a.n, a.state);
   k_adam<<<grid, 256, 0, st>>>(a);
   k_step_end<<<1, 1, 0, st>>>(a.state, a.steps, a.n_groups, a.mixed);
+  count_launches(a.mixed ? 3 : 2);
   return cudaGetLastError();
 }
 

@@ -5,7 +5,17 @@
 #include <cstdio>
 #include <cstring>
 
+#include <atomic>
+#include <vector>
+
 #include "kernels.cuh"
+
+namespace snk {
+std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace snk
+
+constexpr int kStages = 5;
 
 struct snk_ctx {
   int device = 0;
@@ -20,7 +30,41 @@ struct snk_ctx {
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
+  // stage timing (diagnostics)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> recorded;
+  size_t ev_used = 0;
 };
+
+namespace {
+cudaEvent_t next_event(snk_ctx *c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+// Records the start of a stage; stage_end() records its end.
+struct StageMark {
+  snk_ctx *c;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageMark(snk_ctx *c_, int s, cudaStream_t st_) : c(c_), stage(s), st(st_) {
+    if (c->timing && (a = next_event(c))) cudaEventRecord(a, st);
+  }
+  ~StageMark() {
+    if (!a) return;
+    cudaEvent_t b = next_event(c);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    c->recorded.push_back({stage, {a, b}});
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -298,6 +342,7 @@ int snk_ctx_destroy(snk_ctx *ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_views) cudaFree(ctx->d_views);
   if (ctx->h_views) cudaFreeHost(ctx->h_views);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
   return SNK_OK;
 }
@@ -550,8 +595,15 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
   if ((rc = ensure_ws(ctx, B, max_samples_for(win, sampler, B)))) return rc;
   const cudaStream_t st = (cudaStream_t)stream;
-  SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, ctx->rb, ctx->cap_samples, state, st));
-  if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  {
+    StageMark m(ctx, 0, st);
+    SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, ctx->rb, ctx->cap_samples, state,
+                                       st));
+  }
+  {
+    StageMark m(ctx, 1, st);
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
   ca.smp_t = ctx->rb.smp_t;
@@ -565,8 +617,14 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   ca.dsr = ctx->dsr;
   ca.state = state;
   ca.train = 1;
-  SNK_CK(ctx, launch_composite(ca, st));
-  if ((rc = run_field(ctx, model, md, p, state, kBackward, st))) return rc;
+  {
+    StageMark m(ctx, 2, st);
+    SNK_CK(ctx, launch_composite(ca, st));
+  }
+  {
+    StageMark m(ctx, 3, st);
+    if ((rc = run_field(ctx, model, md, p, state, kBackward, st))) return rc;
+  }
   AdamArgs aa{};
   aa.params = p->params;
   aa.params_lp = p->params_lp;
@@ -594,7 +652,10 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   aa.l2 = adam->l2_mlp;
   aa.state = state;
   aa.mixed = model->precision == SNK_MIXED;
-  SNK_CK(ctx, launch_adam(aa, ctx->sm_count, st));
+  {
+    StageMark m(ctx, 4, st);
+    SNK_CK(ctx, launch_adam(aa, ctx->sm_count, st));
+  }
   return SNK_OK;
 }
 
@@ -615,8 +676,15 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
   if ((rc = ensure_ws(ctx, B, max_samples_for(win, sampler, B)))) return rc;
   const cudaStream_t st = (cudaStream_t)stream;
-  SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state, st));
-  if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  {
+    StageMark m(ctx, 0, st);
+    SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state,
+                                       st));
+  }
+  {
+    StageMark m(ctx, 1, st);
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
   ca.smp_t = ctx->rb.smp_t;
@@ -626,7 +694,39 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   ca.B = B;
   ca.out = out;
   ca.state = state;
-  SNK_CK(ctx, launch_composite(ca, st));
+  {
+    StageMark m(ctx, 2, st);
+    SNK_CK(ctx, launch_composite(ca, st));
+  }
+  return SNK_OK;
+}
+
+int64_t snk_launch_count(void) { return snk::g_launches.load(); }
+
+int snk_stage_timing(snk_ctx *ctx, int enable) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  SNK_CK(ctx, cudaDeviceSynchronize());
+  ctx->timing = enable != 0;
+  ctx->recorded.clear();
+  ctx->ev_used = 0;
+  return SNK_OK;
+}
+
+int snk_stage_times(snk_ctx *ctx, double *ms, int64_t *calls, int n) {
+  if (!ctx || !ms || !calls || n < 0) return SNK_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    ms[i] = 0.0;
+    calls[i] = 0;
+  }
+  SNK_CK(ctx, cudaDeviceSynchronize());
+  for (auto &r : ctx->recorded) {
+    float t = 0.f;
+    SNK_CK(ctx, cudaEventElapsedTime(&t, r.second.first, r.second.second));
+    if (r.first < n) {
+      ms[r.first] += t;
+      calls[r.first] += 1;
+    }
+  }
   return SNK_OK;
 }
 

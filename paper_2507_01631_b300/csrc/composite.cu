@@ -153,6 +153,7 @@ cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
   const int64_t threads = (int64_t)a.B * 32;
   k_composite<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 

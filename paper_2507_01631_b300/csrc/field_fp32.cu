@@ -342,6 +342,7 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
   if (grid > max_tiles) grid = max_tiles;
   if (grid <= 0) return cudaSuccess;
   k<<<(unsigned)grid, NT, smem, st>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -396,6 +397,7 @@ cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
   k_encode_scatter<<<(unsigned)blocks, 256, 0, st>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,9 @@
 
 namespace snk {
 
+// Adds n to the library-wide count of launched kernels (snk_launch_count).
+void count_launches(int n);
+
 // Workspace of one ray batch (context-owned, or caller buffers for the stage API).
 struct RayBuffers {
   float *ray_od;       // [6][B]

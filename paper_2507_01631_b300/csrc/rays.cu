@@ -352,6 +352,7 @@ cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinP
   k_samples<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n, rb.excl,
                                                                 rb.block_tot, nb, B, win, smp, state, rb.seg_off,
                                                                 rb.smp_t, rb.smp_dt, rb.smp_xyz);
+  count_launches(4);
   return cudaGetLastError();
 }
 

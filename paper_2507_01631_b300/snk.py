@@ -90,7 +90,11 @@ SIGNATURES = {
     "snk_render": (c_int, [_P, POINTER(SnkModel), POINTER(SnkWindow), _P, c_int, POINTER(SnkSampler),
                            POINTER(SnkParams), _P, _P, _P]),
     "snk_sync_status": (c_int, [_P, _P, _P]),
+    "snk_launch_count": (c_int64, []),
+    "snk_stage_timing": (c_int, [_P, c_int]),
+    "snk_stage_times": (c_int, [_P, POINTER(c_double), POINTER(c_int64), c_int]),
 }
+STAGES = ("rays_segments_samples", "field_forward", "render_loss_backward", "field_backward", "adam")
 
 _lib = None
 
@@ -224,6 +228,15 @@ class Context:
             cp = (c_void_p * len(cams))(*[ptr(x) for x in crops])
         self.call("snk_set_views", arr, len(cams), cp, stream_handle(stream))
         self._keep = [arr, crops]
+
+    def stage_timing(self, enable=True):
+        self.call("snk_stage_timing", 1 if enable else 0)
+
+    def stage_times(self):
+        ms = (c_double * 5)()
+        calls = (c_int64 * 5)()
+        self.call("snk_stage_times", ms, calls, 5)
+        return {n: (ms[i], calls[i]) for i, n in enumerate(STAGES)}
 
     def sync_status(self, state, stream=None):
         return self.lib.snk_sync_status(self.h, ptr(state), stream_handle(stream))

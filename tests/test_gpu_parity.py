@@ -3,7 +3,7 @@
 Bit-exact: rays (binary32 rounding of the binary64 camera), acceptance,
 segment tiles and bounds, samples per segment, sample positions, hash entry
 indices.  Floats: rendered RGB and depth within rel 1e-5 of the oracle (with
-a floor of rel x max|value| for near-zero entries); gradients within 1e-4
+a floor of rel x max|value| for near-zero entries); gradients within 5e-4
 norm-wise per tensor (binary32 accumulation and atomic order)."""
 import ctypes
 
