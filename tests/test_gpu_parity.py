@@ -203,6 +203,36 @@ def test_mlp_forward_and_backward(ctx, name, n_rays):
     at_, ac_ = OS.unflatten(cfg, abs_grad)
     x = feat_h[idx].astype(np.float64)
     dd = dout_h[idx].astype(np.float64)
+    # A ReLU mask is a decision taken by a float: where a pre-activation lies within binary32
+    # rounding of zero (|z| < 1e-5 sum|w x|) the two precisions may decide differently.  Such
+    # samples get a zero upstream gradient on both sides, so their masks cannot matter.
+    amb = np.zeros(cap, bool)
+    amb_r = np.zeros(len(idx), bool)
+    for k in range(case.w.n_slots):
+        m = smp.slot == k
+        if not m.any():
+            continue
+        col = (cols[0] if cfg.shared_colour else cols[k]) if cfg.colour else None
+        _, _, acts = mlp.forward(x[m], tiles[k][1], col)
+        gp = acts["geo_pre"]
+        hidden = [(acts["x0"], tiles[k][1][0], gp[0]), (np.maximum(gp[0], 0), tiles[k][1][1], gp[1])]
+        if col is not None:
+            cp = acts["col_pre"]
+            hidden += [(acts["g"], col[0], cp[0]), (np.maximum(cp[0], 0), col[1], cp[1])]
+        bad = np.zeros(int(m.sum()), bool)
+        for h, Wm, z in hidden:            # the ReLU layers; output layers have no mask
+            bad |= np.any(np.abs(z) < 1e-5 * (np.abs(h) @ np.abs(Wm).T), axis=1)
+        amb_r[np.flatnonzero(m)[bad]] = True
+    amb[idx[amb_r]] = True
+    dout_h[amb] = 0.0
+    dd[amb_r] = 0.0
+    dout.copy_(torch.from_numpy(dout_h))
+    grads.zero_()
+    ctx.call("snk_mlp_backward", ctypes.byref(model), ctypes.byref(ps), snk.ptr(feat), snk.ptr(g["dev"]["state"]),
+             cap, snk.ptr(dout), snk.ptr(dfeat), None)
+    torch.cuda.synchronize()
+    gdf = dfeat.cpu().numpy().reshape(cap, IN)[idx]
+    gg = grads.cpu().numpy().astype(np.float64)
     for k in range(case.w.n_slots):
         m = smp.slot == k
         if not m.any():
