@@ -67,21 +67,25 @@ def mlp_flops_per_sample(w):
 
 
 def field_backward_work(w, precision):
-    """Algorithmic FLOPs and bytes per sample of the fused field backward:
-    recomputed MLP forward + input gradients + weight gradients (3 x the
-    forward MACs), the 8-corner gather of L levels x F features and the
-    8-corner scatter-add (read + write of F binary32 per corner)."""
+    """Algorithmic FLOPs and bytes per sample of the fused field backward.
+    FLOPs: recomputed MLP forward + input gradients + weight gradients (3 x the
+    forward MACs x 2).  Bytes: binary32 path re-gathers the 8 corners of L
+    levels x F features (4 B each); the mixed path reads its stored BF16
+    features instead (2 B x L*F); both read xyz (12 B) and the upstream
+    gradient (16 B) and scatter-add 8 corners x L x F binary32 (read + write)."""
     fl = 3 * mlp_flops_per_sample(w)
-    tbytes = 2 if precision == "mixed" else 4
-    gather = w.L * 8 * w.F * tbytes
+    feat = w.L * 8 * w.F * 4 if precision == "fp32" else 2 * max(16, w.L * w.F)
     scatter = w.L * 8 * w.F * 4 * 2
-    stream = 12 + 16  # xyz in, (dsigma, drgb) in
-    return fl, gather + scatter + stream
+    return fl, feat + scatter + 12 + 16
 
 
 def field_forward_work(w, precision):
-    tbytes = 2 if precision == "mixed" else 4
-    return mlp_flops_per_sample(w), w.L * 8 * w.F * tbytes + 12 + 16
+    """FLOPs: the MLP forward.  Bytes: the 8-corner gather of L x F table
+    entries (4 B binary32, 2 B FP16), xyz in, (sigma, rgb) out, and for the
+    mixed path the BF16 features written for the backward."""
+    if precision == "fp32":
+        return mlp_flops_per_sample(w), w.L * 8 * w.F * 4 + 12 + 16
+    return mlp_flops_per_sample(w), w.L * 8 * w.F * 2 + 12 + 16 + 2 * max(16, w.L * w.F)
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -317,19 +321,27 @@ def run_ours(args, w):
             fl, by = field_forward_work(w, args.precision)
         else:
             fl, by = 0, 0
+        sm_max = pk.get("sm_max_mhz", 2032.0)
         if args.precision == "fp32" and fl:
-            sm_clk = (clk.get("sm_mhz") or pk.get("sm_max_mhz", 2032.0))
-            peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+            peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
             achieved = fl * per_step_samples / per_launch_s / 1e12
             roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived)" % pk.get("sm_max_mhz", 2032.0),
-                    "sm_mhz_median": sm_clk}
+                    "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived)" % sm_max}
         elif fl:
-            achieved = by * per_step_samples / per_launch_s / 1e9
-            roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                    "peak_source": "%s hbm_gbs" % pk["source"]}
+            gbs = by * per_step_samples / per_launch_s / 1e9
+            tfl = fl * per_step_samples / per_launch_s / 1e12
+            hbm = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                   "frac": gbs / pk["hbm_gbs"], "peak_source": "%s hbm_gbs" % pk["source"]}
+            ten = {"bound": "tensor", "achieved": tfl, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                   "frac": tfl / pk["bf16_tflops_sustained"],
+                   "peak_source": "%s bf16_tflops_sustained" % pk["source"]}
+            main, other = (hbm, ten) if hbm["frac"] >= ten["frac"] else (ten, hbm)
+            roof = dict(main)
+            roof.update({"kernel": name, "traffic": None, "other_bound": other})
+        else:
+            roof = {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None}
         roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
 
     cpu = None

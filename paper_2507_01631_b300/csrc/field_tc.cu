@@ -1,8 +1,580 @@
-// Mixed-precision field path (FP16 tables, BF16 MLP on the tensor cores).
+// S3 + S4 (+ S7b, S7c), mixed precision on the 5th-generation tensor cores.
+//
+// Forward (per 128-sample tile, 256 threads): gather the FP16 hash-table
+// features of every level (Sec. 4.1, NGP) and interpolate them in FP32, store
+// them as BF16 into shared memory, then run the density MLP and the shared
+// colour MLP (Sec. 4.1) as a chain of tcgen05 MMAs, M = 128 samples, BF16
+// operands in shared memory, FP32 accumulators in tensor memory.  Each
+// epilogue (ReLU, BF16 cast) goes tensor memory -> registers -> shared memory
+// and feeds the next MMA.  The BF16 features of the tile are also written to
+// global memory (64 bytes per sample) so that the backward does not re-gather
+// 512 bytes per sample from the tables.
+//
+// Backward (per tile, 256 threads, one CTA per SM): reload the features,
+// recompute the MLP activations, then per layer two MMAs: the input gradient
+// dX = delta * W (W read MN-major from the same shared buffer the forward
+// reads K-major) and the weight gradient dW += delta^T * X (both operands read
+// MN-major from the sample-major buffers; the output rows of dW are padded to
+// M = 128 and the padding rows are never read).  The weight gradients stay in
+// tensor memory for the whole persistent loop and are added to the FP32
+// gradient buffer when the CTA moves to another slot and at exit.  The
+// feature gradients are scatter-added into the FP32 table gradients with
+// fire-and-forget float2 atomics.
+//
+// All mbarrier waits are bounded in time; a wait that gives up sets the
+// timeout status bit, stops the tile loop of the CTA, waits (bounded) for the
+// tensor core and frees the tensor memory before returning.
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace snk {
+namespace {
 
-cudaError_t launch_field_tc(const FieldArgs &, int, cudaStream_t) { return cudaErrorNotSupported; }
+constexpr int TM = 128;  // samples per tile = MMA M
+constexpr int TT = 256;  // threads per CTA
+
+template <int IN, bool BWD>
+struct L {
+  static constexpr int INP = IN < 16 ? 16 : IN;  // layer-1 K padded to the MMA K step
+  // deltas first: the padded MN-major reads of dW run up to 32 KB past a delta
+  // buffer and must stay inside the allocation
+  static constexpr int DA = 0;                                 // [128 x 64]
+  static constexpr int DB = BWD ? DA + TM * 64 * 2 : 0;        // [128 x 64]
+  static constexpr int DG = BWD ? DB + TM * 64 * 2 : 0;        // [128 x 16]
+  static constexpr int D3 = BWD ? DG + TM * 16 * 2 : 0;        // [128 x 16]
+  static constexpr int X0 = BWD ? D3 + TM * 16 * 2 : 0;        // [128 x INP]
+  static constexpr int X1 = X0 + TM * INP * 2;                 // h1  [128 x 64]
+  static constexpr int X2 = X1 + TM * 64 * 2;                  // h2
+  static constexpr int X3 = X2 + TM * 64 * 2;                  // g   [128 x 16]
+  static constexpr int X4 = BWD ? X3 + TM * 16 * 2 : X1;       // c1 (forward reuses h1's buffer)
+  static constexpr int X5 = BWD ? X4 + TM * 64 * 2 : X2;       // c2
+  static constexpr int W1 = BWD ? X5 + TM * 64 * 2 : X3 + TM * 16 * 2;  // [64 x INP]
+  static constexpr int W2 = W1 + 64 * INP * 2;                 // [64 x 64]
+  static constexpr int W3 = W2 + 64 * 64 * 2;                  // [16 x 64]
+  static constexpr int V1 = W3 + 16 * 64 * 2;                  // [64 x 16]
+  static constexpr int V2 = V1 + 64 * 16 * 2;                  // [64 x 64]
+  static constexpr int V3 = V2 + 64 * 64 * 2;                  // [16 x 64]
+  static constexpr int END = V3 + 16 * 64 * 2;
+  static constexpr int SMEM = END + 64;                        // + mbarrier and TMEM address
+  static constexpr uint32_t TCOLS = BWD ? 512 : 64;
+  // tensor-memory columns of the backward
+  static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+__device__ __forceinline__ float2 unpack_bf16(uint32_t u) {
+  __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162 *>(&u);
+  return __bfloat1622float2(v);
+}
+
+// D[128 x N] = A[128 x K] * B^T, A K-major (128 rows), B = weights [N x K] K-major (N rows).
+__device__ __forceinline__ void mma_fwd(uint32_t d, uint32_t a, uint32_t b, int K, int N) {
+  const uint32_t id = tc::idesc_bf16(TM, N, 0, 0);
+  for (int j = 0; j < K / 16; ++j)
+    tc::mma_bf16(d, tc::desc(a + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+                 tc::desc(b + j * 2 * (N / 8) * 128, (N / 8) * 128, 128), id, j > 0);
+}
+
+// D[128 x N] = delta[128 x K] * W, delta K-major, W stored [K rows x N] and read MN-major.
+__device__ __forceinline__ void mma_dx(uint32_t d, uint32_t delta, uint32_t w, int K, int N) {
+  const uint32_t id = tc::idesc_bf16(TM, N, 0, 1);
+  for (int j = 0; j < K / 16; ++j)
+    tc::mma_bf16(d, tc::desc(delta + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+                 tc::desc(w + j * 2 * 128, 128, (K / 8) * 128), id, j > 0);
+}
+
+// D[128 (rows = output units, padded) x N] (+)= delta^T * X over the 128 samples; both read MN-major.
+__device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, int N, uint32_t accumulate) {
+  const uint32_t id = tc::idesc_bf16(TM, N, 1, 1);
+  for (int j = 0; j < TM / 16; ++j)
+    tc::mma_bf16(d, tc::desc(delta + j * 2 * 128, 128, (TM / 8) * 128), tc::desc(x + j * 2 * 128, 128, (TM / 8) * 128),
+                 id, (j > 0) || accumulate);
+}
+
+// Copy a row-major [rows x cols] bf16 matrix from global into the core layout (R = rpad rows,
+// C = cpad columns), zero-padding, all threads.
+__device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, int rows, int cols, int rpad, int cpad) {
+  for (int e = threadIdx.x; e < rpad * cpad; e += blockDim.x) {
+    const int r = e / cpad, c = e % cpad;
+    const uint16_t v = (r < rows && c < cols) ? src[r * cols + c] : (uint16_t)0;
+    *reinterpret_cast<uint16_t *>(dst + tc::core_off(r, c, rpad)) = v;
+  }
+}
+
+// Epilogue of a [128 x 64] accumulator: this thread's row r and its 32-column half.
+// mode 0: ReLU -> out;  mode 1: out = v * (mask > 0)  (mask from a [128 x 64] activation buffer).
+template <int MODE>
+__device__ __forceinline__ void epi64(uint32_t taddr, uint8_t *out, const uint8_t *mask, int r, int ch) {
+  float v[32];
+  {
+    float a[16], b[16];
+    tc::ld16(taddr + ch * 32, a);
+    tc::ld16(taddr + ch * 32 + 16, b);
+    tc::wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      v[i] = a[i];
+      v[16 + i] = b[i];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = ch * 32 + q * 8;
+    const uint32_t off = tc::core_off(r, c, TM);
+    uint4 m4 = make_uint4(0, 0, 0, 0);
+    if (MODE == 1) m4 = *reinterpret_cast<const uint4 *>(mask + off);
+    const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+    uint32_t o[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float x0 = v[q * 8 + 2 * p], x1 = v[q * 8 + 2 * p + 1];
+      if (MODE == 0) {
+        x0 = fmaxf(x0, 0.f);
+        x1 = fmaxf(x1, 0.f);
+      } else {
+        const float2 mk = unpack_bf16(mw[p]);
+        x0 = mk.x > 0.f ? x0 : 0.f;
+        x1 = mk.y > 0.f ? x1 : 0.f;
+      }
+      o[p] = pack_bf16(x0, x1);
+    }
+    *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+// Store 16 floats as one bf16 row segment of a [128 x 16] buffer.
+__device__ __forceinline__ void store16(uint8_t *buf, int r, const float (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    uint32_t o[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) o[p] = pack_bf16(v[q * 8 + 2 * p], v[q * 8 + 2 * p + 1]);
+    *reinterpret_cast<uint4 *>(buf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
+
+template <int IN, int G, bool COL, bool BWD>
+__global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
+  using Y = L<IN, BWD>;
+  constexpr int INP = Y::INP;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + Y::END);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Y::END + 16);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int r = 32 * (warp & 3) + lane;  // TMEM lane = tile row of this thread
+  const int ch = warp >> 2;             // column half
+  const snk_state *st = a.state;
+  snk_state *st_rw = const_cast<snk_state *>(a.state);
+  const ModelDev &m = a.m;
+  const GridParams &gp = m.grid;
+  const uint32_t s0 = tc::smem_u32(sm);
+
+  if (t == 0) {
+    tc::mbar_init(mbar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, Y::TCOLS);
+  // zero every operand buffer once (padding columns are never written again)
+  for (int i = t; i < Y::END / 16; i += TT) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  uint32_t phase = 0;
+  bool abort = false;
+
+  int64_t r0 = 0, r1 = st->slot_base[kMaxSlots];
+  if (a.slot_only >= 0) {
+    r0 = st->slot_base[a.slot_only];
+    r1 = r0 + st->slot_count[a.slot_only];
+  }
+  if (r1 > a.S) r1 = a.S;
+  const int64_t n_tiles = r1 > r0 ? (r1 - r0 + TM - 1) / TM : 0;
+  int cur_slot = -1;
+  bool fresh = true;  // next dW MMAs start the accumulators
+
+  // all threads: wait for the MMAs committed last; CTA-uniform result
+  auto sync_mma = [&]() -> bool {
+    const bool ok = tc::mbar_wait(mbar, phase);
+    if (ok) phase ^= 1u;
+    tc::fence_after_sync();
+    return __syncthreads_or(!ok) == 0;
+  };
+  // after an epilogue: make smem writes visible to the tensor core and TMEM reads ordered
+  auto handoff = [&]() {
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+
+  // add the dW accumulators of slot k to the FP32 gradients (BWD only)
+  auto flush = [&](int k) {
+    if (!BWD) return;
+    float *gs = a.grads + (int64_t)k * m.tile_params;
+    float *gc = a.grads + m.colour_base + (m.shared_colour ? 0 : (int64_t)k * m.colour_params);
+    struct R {
+      uint32_t col;
+      int ncol, out, in;
+      float *dst;
+    };
+    const R regs[6] = {{Y::C_W1, INP, 64, IN, gs + m.w1}, {Y::C_W2, 64, 64, 64, gs + m.w2},
+                       {Y::C_W3, 64, G, 64, gs + m.w3},   {Y::C_V1, 16, 64, G, gc + m.v1},
+                       {Y::C_V2, 64, 64, 64, gc + m.v2},  {Y::C_V3, 64, 3, 64, gc + m.v3}};
+    const int nreg = COL ? 6 : 3;
+    for (int q = 0; q < nreg; ++q) {
+      const R &g = regs[q];
+      if ((warp & 3) >= 2) continue;  // rows >= 64 are padding
+      for (int c0 = ch * 16; c0 < g.ncol; c0 += 32) {
+        float v[16];
+        tc::ld16(trow + g.col + c0, v);
+        tc::wait_ld();
+        if (r < g.out) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c0 + i < g.in && v[i] != 0.f) atomicAdd(g.dst + (int64_t)r * g.in + c0 + i, v[i]);
+        }
+      }
+    }
+    fresh = true;
+  };
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !abort; tile += gridDim.x) {
+    const int64_t ts = r0 + tile * TM;
+    const int slot = slot_of(st, ts);
+    if (slot < 0) continue;
+    if (slot != cur_slot) {
+      if (cur_slot >= 0) flush(cur_slot);
+      __syncthreads();
+      const uint16_t *P = a.params_lp + (int64_t)slot * m.tile_params;
+      const uint16_t *C = a.params_lp + m.colour_base + (m.shared_colour ? 0 : (int64_t)slot * m.colour_params);
+      load_weights(sm + Y::W1, P + m.w1, 64, IN, 64, INP);
+      load_weights(sm + Y::W2, P + m.w2, 64, 64, 64, 64);
+      load_weights(sm + Y::W3, P + m.w3, G, 64, 16, 64);
+      if (COL) {
+        load_weights(sm + Y::V1, C + m.v1, 64, G, 64, 16);
+        load_weights(sm + Y::V2, C + m.v2, 64, 64, 64, 64);
+        load_weights(sm + Y::V3, C + m.v3, 3, 64, 16, 64);
+      }
+      cur_slot = slot;
+      handoff();
+    }
+    const int64_t slot_end = (int64_t)st->slot_base[slot] + st->slot_count[slot];
+    const int64_t idx = ts + r;
+    const bool valid = idx < slot_end && idx < r1;
+    uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(TM * INP);
+
+    // ---- features ----
+    if (!BWD) {
+      const int s = t & (TM - 1), half = t >> 7;
+      const int64_t sidx = ts + s;
+      const bool sval = sidx < slot_end && sidx < r1;
+      float xyz[3] = {0.f, 0.f, 0.f};
+      if (sval) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[sidx * 3 + q];
+      }
+      const __half2 *tab0 = reinterpret_cast<const __half2 *>(a.params_lp + (int64_t)slot * m.tile_params);
+      for (int l = half; l < gp.L; l += 2) {
+        const int N = gp.res[l];
+        const bool dense = gp.dense[l] != 0;
+        int ci[3];
+        float fr[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
+        const __half2 *tab = tab0 + gp.offset[l];
+        float f0 = 0.f, f1 = 0.f;
+        if (sval) {
+          __half2 hv[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            hv[c] = __ldg(tab + grid_index(ci[0] + (c & 1), ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                           (uint32_t)gp.T - 1u));
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
+                            ((c & 4) ? fr[2] : 1.0f - fr[2]);
+            const float2 v = __half22float2(hv[c]);
+            f0 = fmaf(w, v.x, f0);
+            f1 = fmaf(w, v.y, f1);
+          }
+        }
+        *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = pack_bf16(f0, f1);
+      }
+      __syncthreads();
+      // the tile's features, in the shared-memory layout, for the backward
+      for (int i = t; i < TM * INP * 2 / 16; i += TT)
+        reinterpret_cast<uint4 *>(ftile)[i] = reinterpret_cast<const uint4 *>(sm + Y::X0)[i];
+    } else {
+      for (int i = t; i < TM * INP * 2 / 16; i += TT)
+        reinterpret_cast<uint4 *>(sm + Y::X0)[i] = reinterpret_cast<const uint4 *>(ftile)[i];
+    }
+    handoff();
+
+    // ---- forward MLP ----
+    if (t == 0) {
+      mma_fwd(tmem, s0 + Y::X0, s0 + Y::W1, INP, 64);
+      tc::commit(mbar);
+    }
+    abort = !sync_mma();
+    if (abort) break;
+    epi64<0>(trow, sm + Y::X1, nullptr, r, ch);
+    handoff();
+    if (t == 0) {
+      mma_fwd(tmem, s0 + Y::X1, s0 + Y::W2, 64, 64);
+      tc::commit(mbar);
+    }
+    abort = !sync_mma();
+    if (abort) break;
+    epi64<0>(trow, sm + Y::X2, nullptr, r, ch);
+    handoff();
+    if (t == 0) {
+      mma_fwd(tmem, s0 + Y::X2, s0 + Y::W3, 64, 16);
+      tc::commit(mbar);
+    }
+    abort = !sync_mma();
+    if (abort) break;
+    float g[16];
+    float rgb[3] = {0.f, 0.f, 0.f};
+    if (ch == 0) {
+      tc::ld16(trow, g);
+      tc::wait_ld();
+      store16(sm + Y::X3, r, g);
+      if (!COL) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rgb[k] = sigm(g[1 + k]);
+      }
+    }
+    handoff();
+    if (COL) {
+      if (t == 0) {
+        mma_fwd(tmem, s0 + Y::X3, s0 + Y::V1, 16, 64);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      epi64<0>(trow, sm + Y::X4, nullptr, r, ch);
+      handoff();
+      if (t == 0) {
+        mma_fwd(tmem, s0 + Y::X4, s0 + Y::V2, 64, 64);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      epi64<0>(trow, sm + Y::X5, nullptr, r, ch);
+      handoff();
+      if (t == 0) {
+        mma_fwd(tmem, s0 + Y::X5, s0 + Y::V3, 64, 16);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      if (ch == 0) {
+        float o[16];
+        tc::ld16(trow, o);
+        tc::wait_ld();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rgb[k] = sigm(o[k]);
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+
+    if (!BWD) {
+      if (ch == 0 && valid)
+        reinterpret_cast<float4 *>(a.sigma_rgb)[idx] = make_float4(__expf(g[0]), rgb[0], rgb[1], rgb[2]);
+      continue;
+    }
+
+    // ---- backward ----
+    // output deltas (the upstream gradient already carries the loss scale)
+    if (ch == 0) {
+      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) d = reinterpret_cast<const float4 *>(a.dsr)[idx];
+      const float dg0 = d.x * __expf(fminf(fmaxf(g[0], -15.f), 15.f));
+      const float d3[3] = {d.y * rgb[0] * (1.f - rgb[0]), d.z * rgb[1] * (1.f - rgb[1]), d.w * rgb[2] * (1.f - rgb[2])};
+      float row[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) row[i] = 0.f;
+      if (COL) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) row[k] = d3[k];
+        store16(sm + Y::D3, r, row);
+        g[0] = dg0;  // keep dsigma's contribution to dg_0 for later
+      } else {
+        row[0] = dg0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) row[1 + k] = d3[k];
+        store16(sm + Y::DG, r, row);
+      }
+    }
+    handoff();
+    const uint32_t acc = fresh ? 0u : 1u;
+    if (COL) {
+      // dc2 = delta3 * V3, dV3 += delta3^T c2
+      if (t == 0) {
+        mma_dx(tmem, s0 + Y::D3, s0 + Y::V3, 16, 64);
+        mma_dw(tmem + Y::C_V3, s0 + Y::D3, s0 + Y::X5, 64, acc);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      epi64<1>(trow, sm + Y::DA, sm + Y::X5, r, ch);
+      handoff();
+      // dc1 = delta_c2 * V2, dV2 += delta_c2^T c1
+      if (t == 0) {
+        mma_dx(tmem, s0 + Y::DA, s0 + Y::V2, 64, 64);
+        mma_dw(tmem + Y::C_V2, s0 + Y::DA, s0 + Y::X4, 64, acc);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      epi64<1>(trow, sm + Y::DB, sm + Y::X4, r, ch);
+      handoff();
+      // dg = delta_c1 * V1 (+ dsigma term), dV1 += delta_c1^T g
+      if (t == 0) {
+        mma_dx(tmem, s0 + Y::DB, s0 + Y::V1, 64, 16);
+        mma_dw(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, 16, acc);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      if (ch == 0) {
+        float dg[16];
+        tc::ld16(trow, dg);
+        tc::wait_ld();
+        dg[0] += g[0];
+        store16(sm + Y::DG, r, dg);
+      }
+      handoff();
+    }
+    // dh2 = delta_g * W3 (masked by h2), dW3 += delta_g^T h2
+    if (t == 0) {
+      mma_dx(tmem, s0 + Y::DG, s0 + Y::W3, 16, 64);
+      mma_dw(tmem + Y::C_W3, s0 + Y::DG, s0 + Y::X2, 64, acc);
+      tc::commit(mbar);
+    }
+    abort = !sync_mma();
+    if (abort) break;
+    epi64<1>(trow, sm + Y::DA, sm + Y::X2, r, ch);
+    handoff();
+    // dh1 = delta_h2 * W2 (masked by h1), dW2 += delta_h2^T h1
+    if (t == 0) {
+      mma_dx(tmem, s0 + Y::DA, s0 + Y::W2, 64, 64);
+      mma_dw(tmem + Y::C_W2, s0 + Y::DA, s0 + Y::X1, 64, acc);
+      tc::commit(mbar);
+    }
+    abort = !sync_mma();
+    if (abort) break;
+    epi64<1>(trow, sm + Y::DB, sm + Y::X1, r, ch);
+    handoff();
+    // dfeat = delta_h1 * W1, dW1 += delta_h1^T feat
+    if (t == 0) {
+      mma_dx(tmem, s0 + Y::DB, s0 + Y::W1, 64, INP);
+      mma_dw(tmem + Y::C_W1, s0 + Y::DB, s0 + Y::X0, INP, acc);
+      tc::commit(mbar);
+    }
+    abort = !sync_mma();
+    if (abort) break;
+    fresh = false;
+    // ---- scatter dfeat into the table gradients ----
+    const int c0 = ch * 16;
+    if (c0 < IN) {
+      float df[16];
+      tc::ld16(trow + c0, df);
+      tc::wait_ld();
+      if (valid) {
+        float xyz[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[idx * 3 + q];
+        float2 *gt0 = reinterpret_cast<float2 *>(a.grads + (int64_t)slot * m.tile_params);
+        const int l0 = c0 / 2, l1 = min(gp.L, l0 + 8);
+        for (int l = l0; l < l1; ++l) {
+          const int N = gp.res[l];
+          const bool dense = gp.dense[l] != 0;
+          int ci[3];
+          float fr[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
+          const float d0 = df[2 * (l - l0)], d1 = df[2 * (l - l0) + 1];
+          float2 *gt = gt0 + gp.offset[l];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t e = grid_index(ci[0] + (c & 1), ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                          (uint32_t)gp.T - 1u);
+            const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
+                            ((c & 4) ? fr[2] : 1.0f - fr[2]);
+            atomicAdd(gt + e, make_float2(w * d0, w * d1));
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+
+  if (abort) {
+    if (t == 0) atomicOr(&st_rw->status, kStatusTimeout);
+    tc::mbar_wait(mbar, phase);  // bounded: let any MMA still in flight finish before freeing TMEM
+  } else if (BWD && cur_slot >= 0) {
+    flush(cur_slot);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
+}
+
+template <int IN, int G, bool COL, bool BWD>
+cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
+  using Y = L<IN, BWD>;
+  auto k = k_field_tc<IN, G, COL, BWD>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int64_t max_tiles = (a.S + TM - 1) / TM;
+  const int per_sm = BWD ? 1 : 2;
+  int64_t grid = (int64_t)sm_count * per_sm;
+  if (grid > max_tiles) grid = max_tiles;
+  if (grid <= 0) return cudaSuccess;
+  k<<<(unsigned)grid, TT, Y::SMEM, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int IN, int G, bool COL>
+cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st) {
+  if (a.mode == kBackward) return launch_t<IN, G, COL, true>(a, sm_count, st);
+  return launch_t<IN, G, COL, false>(a, sm_count, st);
+}
+
+template <int IN>
+cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st) {
+  if (a.m.colour) return launch_mode<IN, 16, true>(a, sm_count, st);
+  return launch_mode<IN, 4, false>(a, sm_count, st);
+}
+
+}  // namespace
+
+cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st) {
+  if (a.mode == kEncodeOnly || a.feat_lp == nullptr || a.params_lp == nullptr) return cudaErrorInvalidValue;
+  switch (a.m.in_dim) {
+    case 8: return launch_in<8>(a, sm_count, st);
+    case 16: return launch_in<16>(a, sm_count, st);
+    case 32: return launch_in<32>(a, sm_count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 }  // namespace snk

@@ -51,6 +51,7 @@ struct FieldArgs {
   float *sigma_rgb;           // forward output [S][4]
   const float *dsr;           // backward input [S][4]
   float *dfeat_out;           // backward: write dfeat here instead of scattering, or null
+  uint16_t *feat_lp;          // mixed path: BF16 features per 128-sample tile (forward writes, backward reads)
   const snk_state *state;
   int64_t S;                  // extent of the slot-major arrays
   int32_t slot_only;          // -1: every slot; k: only slot k (per-tile launches)

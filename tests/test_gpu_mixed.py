@@ -1,0 +1,131 @@
+"""Mixed-precision path (FP16 tables, BF16 MLP on the tcgen05 tensor cores, FP32
+accumulation, loss scaling) against the FP64 oracle, through the C ABI.
+
+The oracle runs on the parameters the mixed model computes with: its working
+copy (tables rounded to FP16, MLP weights to BF16).  Tolerances: rendered RGB
+and depth rel 2e-3 (floor 2e-3 x max), gradients 5e-3 norm-wise per tensor."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2507_01631_b300 import build, snk
+from paper_2507_01631_b300.trainer import Trainer, model_from_workload
+from oracle import step as OS
+from gpu_util import GRAD_REL_MIXED, RGB_REL_MIXED, close, make_case, normwise
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    c = snk.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def working_copy(params, cfg):
+    """FP64 values of the mixed model's working copy of binary32 parameters."""
+    p = params.astype(np.float64).copy()
+    for a, b, mlp_a in OS.group_ranges(cfg):
+        p[a:mlp_a] = params[a:mlp_a].astype(np.float16).astype(np.float64)
+        p[mlp_a:b] = torch.from_numpy(params[mlp_a:b].copy()).to(torch.bfloat16).to(torch.float64).numpy()
+    return p
+
+
+def _trainer(ctx, case, seed=5, render=0):
+    w = case.w
+    crops = [dev(t.astype(np.float32)) for t in case.targets] if case.targets is not None else None
+    ctx.set_views(case.cams, crops)
+    model = model_from_workload(w, snk.SNK_MIXED)
+    sp = snk.sampler_struct(w.K_ray, w.K_min, w.K_max, render, seed, 0)
+    tr = Trainer(ctx, model, snk.window_struct(w.window()), sp, case.params)
+    tr._crops = crops
+    return tr
+
+
+MIXED_CASES = [("tiny_tile", 96, None), ("tiny_window", 160, None), ("tile256_fp32", 512, None),
+               ("tile512_full", 512, 48), ("window2x2_full", 512, 48)]
+
+
+@pytest.mark.parametrize("name,n_rays,crop", MIXED_CASES)
+def test_train_step_mixed_matches_oracle(ctx, name, n_rays, crop):
+    case = make_case(name, n_rays=n_rays, crop=crop, table_scale=0.3)
+    tr = _trainer(ctx, case)
+    B = n_rays
+    out = torch.zeros(B * 5, dtype=torch.float32, device="cuda")
+    tr.train_step(dev(case.pix.view(np.int32)), out)
+    assert ctx.sync_status(tr.state) == snk.SNK_OK
+    st = tr.read_state()
+    n = len(case.params)
+    wc = working_copy(case.params, case.cfg)
+    ref = OS.train_step(case.cfg, wc, np.zeros(n), np.zeros(n), [0] * case.cfg.n_optimisers(), case.cams,
+                        case.w.window(), case.pix, case.targets, 5, 0)
+    assert st["n_samples"] == int(ref.seg.ray_off[-1]) and st["n_accepted"] == int(ref.seg.ray_ok.sum())
+    go = out.cpu().numpy().reshape(B, 5)
+    for nm, a, b in [("rgb", go[:, :3], ref.rgb), ("depth", go[:, 3], ref.depth), ("opacity", go[:, 4], ref.opacity)]:
+        ok, err = close(a, b, RGB_REL_MIXED)
+        assert ok, (nm, err)
+    # loss = mean (C - gt)^2: an RGB error e changes it by at most 2 sqrt(loss) e
+    e = RGB_REL_MIXED * 2 * max(1.0, np.abs(ref.rgb).max())
+    assert abs(st["loss"] - ref.loss) <= 2 * np.sqrt(ref.loss) * e + 1e-7, (st["loss"], ref.loss)
+    m = tr.m.cpu().numpy().astype(np.float64)
+    for gi, (a, b, mlp_a) in enumerate(OS.group_ranges(case.cfg)):
+        if mlp_a > a:
+            assert normwise(m[a:mlp_a], ref.m[a:mlp_a]) < GRAD_REL_MIXED, ("table", gi, normwise(m[a:mlp_a], ref.m[a:mlp_a]))
+        assert normwise(m[mlp_a:b], ref.m[mlp_a:b]) < GRAD_REL_MIXED, ("mlp", gi, normwise(m[mlp_a:b], ref.m[mlp_a:b]))
+        # parameters with a clearly non-zero gradient move by the oracle's first Adam step
+        pg = tr.params.cpu().numpy().astype(np.float64)[a:b]
+        moved = ref.params[a:b] - wc[a:b]
+        rg = np.abs(ref.grad[a:b])
+        sure = rg > 5e-2 * max(rg.max(), 1e-30)
+        assert np.allclose(pg[sure], case.params[a:b][sure] + moved[sure], rtol=0, atol=1e-5)
+    assert np.all(tr.steps.cpu().numpy() == 1)
+    assert np.all(tr.grads.cpu().numpy() == 0)
+    # the working copy was refreshed from the updated master weights
+    lp = tr.params_lp.cpu()
+    from paper_2507_01631_b300.trainer import low_precision_copy
+    assert torch.equal(lp, low_precision_copy(tr.params.cpu(), tr.lay, tr.model))
+
+
+@pytest.mark.parametrize("name,n_rays", [("tiny_window", 160), ("tile512_full", 400), ("window2x2_full", 600)])
+def test_render_mixed_matches_oracle(ctx, name, n_rays):
+    case = make_case(name, n_rays=n_rays, table_scale=0.3, with_targets=False)
+    tr = _trainer(ctx, case, render=1)
+    out = torch.zeros(n_rays * 5, dtype=torch.float32, device="cuda")
+    tr.render(dev(case.pix.view(np.int32)), out)
+    assert ctx.sync_status(tr.state) == snk.SNK_OK
+    ref = OS.render_rays(case.cfg, working_copy(case.params, case.cfg), case.cams, case.w.window(), case.pix)
+    go = out.cpu().numpy().reshape(n_rays, 5)
+    for nm, a, b in [("rgb", go[:, :3], ref.rgb), ("depth", go[:, 3], ref.depth), ("opacity", go[:, 4], ref.opacity)]:
+        ok, err = close(a, b, RGB_REL_MIXED)
+        assert ok, (nm, err)
+
+
+def test_mixed_training_reduces_the_loss_and_skips_overflow_steps(ctx):
+    """Twenty mixed steps on one tile: finite, decreasing loss.  A loss scale so
+    large that the scaled gradients overflow binary32 makes the step skip
+    (status bit 0), halve the scale and leave the weights unchanged."""
+    case = make_case("tiny_window", n_rays=160, table_scale=1e-4)
+    tr = _trainer(ctx, case)
+    pix = dev(case.pix.view(np.int32))
+    losses = []
+    for i in range(20):
+        tr.train_step(pix)
+        losses.append(tr.read_state()["loss"])
+    assert ctx.sync_status(tr.state) == snk.SNK_OK
+    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
+    before = tr.params.clone()
+    tr.state.view(torch.float32)[1] = 3.0e38
+    tr.train_step(pix)
+    st = tr.read_state()
+    assert st["status"] & snk.STATUS_OVERFLOW
+    assert st["loss_scale"] == pytest.approx(1.5e38, rel=1e-6)
+    assert torch.equal(tr.params, before)
+    assert ctx.sync_status(tr.state) == snk.SNK_ERR_OVERFLOW
