@@ -166,23 +166,28 @@ def cpu_threads():
         return 1
 
 
-def make_inputs(w):
+def make_inputs(w, n_grid_params):
+    """Cameras, target images and initial parameters of the workload;
+    n_grid_params = table parameters per tile (from the caller's layout)."""
     cams = W.cameras(w)
     targets = synth.smooth_images(w.seed + 17, w.n_views, w.px, w.px)
-    from oracle import hashgrid  # sizes only
-    lay = hashgrid.layout(w.L, w.F, w.log2_T, w.n_min, w.n_max)
     geo = [(64, w.L * w.F), (64, 64), (w.geo_out, 64)]
     col = [(64, w.geo_out), (64, 64), (3, 64)] if w.colour else []
     n_col = (1 if w.shared_colour else w.n_slots) if w.colour else 0
-    params = W.init_params(lay.n_params, geo, col, w.n_slots, n_col, w.seed)
+    params = W.init_params(n_grid_params, geo, col, w.n_slots, n_col, w.seed)
     return cams, targets, params
+
+
+def oracle_grid_params(w):
+    from oracle import hashgrid
+    return hashgrid.layout(w.L, w.F, w.log2_T, w.n_min, w.n_max).n_params
 
 
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cams, targets, params = make_inputs(w)
+    cams, targets, params = make_inputs(w, oracle_grid_params(w))
     tot_s = tot_t = 0.0
     for i in range(args.warmup):
         oracle_sample(w, cams, targets, params, i, min(32, args.cpu_rays))
@@ -219,11 +224,11 @@ def run_ours(args, w):
     if world > 1:
         dist.barrier()
     precision = snk.SNK_MIXED if args.precision == "mixed" else snk.SNK_FP32
-    cams, targets, params = make_inputs(w)
+    model = model_from_workload(w, precision)
+    cams, targets, params = make_inputs(w, snk.layout(model).grid_params)
     ctx = snk.Context(local)
     crops = [torch.from_numpy(t).cuda() for t in targets]
     ctx.set_views(cams, crops)
-    model = model_from_workload(w, precision)
     sampler = snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, 1234 + rank, 0)
     tr = Trainer(ctx, model, snk.window_struct(w.window()), sampler, params)
     batches_h = [W.batch(w, cams, 50 + i + 1000 * rank).view(np.int32) for i in range(N_BATCHES)]
