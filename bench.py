@@ -70,7 +70,7 @@ def field_backward_work(w, precision):
     """Algorithmic FLOPs and bytes per sample of the fused field backward.
     FLOPs: recomputed MLP forward + input gradients + weight gradients (3 x the
     forward MACs x 2).  Bytes: binary32 path re-gathers the 8 corners of L
-    levels x F features (4 B each); the mixed path reads its stored BF16
+    levels x F features (4 B each); the mixed path reads its stored FP16
     features instead (2 B x L*F); both read xyz (12 B) and the upstream
     gradient (16 B) and scatter-add 8 corners x L x F binary32 (read + write)."""
     fl = 3 * mlp_flops_per_sample(w)
@@ -82,7 +82,7 @@ def field_backward_work(w, precision):
 def field_forward_work(w, precision):
     """FLOPs: the MLP forward.  Bytes: the 8-corner gather of L x F table
     entries (4 B binary32, 2 B FP16), xyz in, (sigma, rgb) out, and for the
-    mixed path the BF16 features written for the backward."""
+    mixed path the FP16 features written for the backward."""
     if precision == "fp32":
         return mlp_flops_per_sample(w), w.L * 8 * w.F * 4 + 12 + 16
     return mlp_flops_per_sample(w), w.L * 8 * w.F * 2 + 12 + 16 + 2 * max(16, w.L * w.F)

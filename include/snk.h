@@ -147,7 +147,7 @@ typedef struct {
 /* Trainable state, all device memory of n_params entries (snk_layout). */
 typedef struct {
     float *params;       /* binary32 master weights */
-    uint16_t *params_lp; /* SNK_MIXED: working copy, FP16 for tables, BF16 for MLP weights; else NULL */
+    uint16_t *params_lp; /* SNK_MIXED: FP16 working copy of all parameters (tables and MLP weights); else NULL */
     float *grads;        /* gradient accumulator; must be zero before a step, zeroed by the step */
     float *adam_m;
     float *adam_v;

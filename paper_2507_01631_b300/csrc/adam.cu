@@ -2,7 +2,7 @@
 // hash table and density MLP) and one per colour MLP, none of them reset when
 // the window moves (Sec. 4.1, 4.4, 4.6).  The update is fused with zeroing
 // the gradient accumulator and, for mixed precision, with refreshing the
-// FP16 table / BF16 weight working copies and with the loss-scale logic:
+// FP16 working copy of tables and weights and with the loss-scale logic:
 // a step whose gradients are not all finite is skipped, the scale halved.
 #include "kernels.cuh"
 
@@ -45,9 +45,7 @@ __global__ void k_adam(const AdamArgs a) {
     a.params[i] = w;
     a.m[i] = m;
     a.v[i] = v;
-    if (a.params_lp) {
-      a.params_lp[i] = mlp ? __bfloat16_as_ushort(__float2bfloat16_rn(w)) : __half_as_ushort(__float2half_rn(w));
-    }
+    if (a.params_lp) a.params_lp[i] = __half_as_ushort(__float2half_rn(w));
   }
 }
 

@@ -27,7 +27,7 @@ struct snk_ctx {
   snk::RayBuffers rb{};
   float *sigma_rgb = nullptr;  // [cap_samples][4]
   float *dsr = nullptr;        // [cap_samples][4]
-  uint16_t *feat_lp = nullptr; // [cap_samples + 128][32] BF16 features of the mixed path
+  uint16_t *feat_lp = nullptr; // [cap_samples + 128][32] FP16 features of the mixed path
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;

@@ -2,11 +2,11 @@
 //
 // Forward (per 128-sample tile, 256 threads): gather the FP16 hash-table
 // features of every level (Sec. 4.1, NGP) and interpolate them in FP32, store
-// them as BF16 into shared memory, then run the density MLP and the shared
-// colour MLP (Sec. 4.1) as a chain of tcgen05 MMAs, M = 128 samples, BF16
+// them as FP16 into shared memory, then run the density MLP and the shared
+// colour MLP (Sec. 4.1) as a chain of tcgen05 MMAs, M = 128 samples, FP16
 // operands in shared memory, FP32 accumulators in tensor memory.  Each
-// epilogue (ReLU, BF16 cast) goes tensor memory -> registers -> shared memory
-// and feeds the next MMA.  The BF16 features of the tile are also written to
+// epilogue (ReLU, FP16 cast) goes tensor memory -> registers -> shared memory
+// and feeds the next MMA.  The FP16 features of the tile are also written to
 // global memory (64 bytes per sample) so that the backward does not re-gather
 // 512 bytes per sample from the tables.
 //
@@ -61,40 +61,40 @@ struct L {
   static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
 };
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+  const __half2 v = __floats2half2_rn(a, b);
   return *reinterpret_cast<const uint32_t *>(&v);
 }
-__device__ __forceinline__ float2 unpack_bf16(uint32_t u) {
-  __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162 *>(&u);
-  return __bfloat1622float2(v);
+__device__ __forceinline__ float2 unpack_h2(uint32_t u) {
+  __half2 v = *reinterpret_cast<__half2 *>(&u);
+  return __half22float2(v);
 }
 
 // D[128 x N] = A[128 x K] * B^T, A K-major (128 rows), B = weights [N x K] K-major (N rows).
 __device__ __forceinline__ void mma_fwd(uint32_t d, uint32_t a, uint32_t b, int K, int N) {
-  const uint32_t id = tc::idesc_bf16(TM, N, 0, 0);
+  const uint32_t id = tc::idesc_f16(TM, N, 0, 0);
   for (int j = 0; j < K / 16; ++j)
-    tc::mma_bf16(d, tc::desc(a + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+    tc::mma_f16(d, tc::desc(a + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
                  tc::desc(b + j * 2 * (N / 8) * 128, (N / 8) * 128, 128), id, j > 0);
 }
 
 // D[128 x N] = delta[128 x K] * W, delta K-major, W stored [K rows x N] and read MN-major.
 __device__ __forceinline__ void mma_dx(uint32_t d, uint32_t delta, uint32_t w, int K, int N) {
-  const uint32_t id = tc::idesc_bf16(TM, N, 0, 1);
+  const uint32_t id = tc::idesc_f16(TM, N, 0, 1);
   for (int j = 0; j < K / 16; ++j)
-    tc::mma_bf16(d, tc::desc(delta + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
+    tc::mma_f16(d, tc::desc(delta + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
                  tc::desc(w + j * 2 * 128, 128, (K / 8) * 128), id, j > 0);
 }
 
 // D[128 (rows = output units, padded) x N] (+)= delta^T * X over the 128 samples; both read MN-major.
 __device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, int N, uint32_t accumulate) {
-  const uint32_t id = tc::idesc_bf16(TM, N, 1, 1);
+  const uint32_t id = tc::idesc_f16(TM, N, 1, 1);
   for (int j = 0; j < TM / 16; ++j)
-    tc::mma_bf16(d, tc::desc(delta + j * 2 * 128, 128, (TM / 8) * 128), tc::desc(x + j * 2 * 128, 128, (TM / 8) * 128),
+    tc::mma_f16(d, tc::desc(delta + j * 2 * 128, 128, (TM / 8) * 128), tc::desc(x + j * 2 * 128, 128, (TM / 8) * 128),
                  id, (j > 0) || accumulate);
 }
 
-// Copy a row-major [rows x cols] bf16 matrix from global into the core layout (R = rpad rows,
+// Copy a row-major [rows x cols] 16-bit matrix from global into the core layout (R = rpad rows,
 // C = cpad columns), zero-padding, all threads.
 __device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, int rows, int cols, int rpad, int cpad) {
   for (int e = threadIdx.x; e < rpad * cpad; e += blockDim.x) {
@@ -135,23 +135,23 @@ __device__ __forceinline__ void epi64(uint32_t taddr, uint8_t *out, const uint8_
         x0 = fmaxf(x0, 0.f);
         x1 = fmaxf(x1, 0.f);
       } else {
-        const float2 mk = unpack_bf16(mw[p]);
+        const float2 mk = unpack_h2(mw[p]);
         x0 = mk.x > 0.f ? x0 : 0.f;
         x1 = mk.y > 0.f ? x1 : 0.f;
       }
-      o[p] = pack_bf16(x0, x1);
+      o[p] = pack_h2(x0, x1);
     }
     *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
   }
 }
 
-// Store 16 floats as one bf16 row segment of a [128 x 16] buffer.
+// Store 16 floats as one FP16 row segment of a [128 x 16] buffer.
 __device__ __forceinline__ void store16(uint8_t *buf, int r, const float (&v)[16]) {
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     uint32_t o[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) o[p] = pack_bf16(v[q * 8 + 2 * p], v[q * 8 + 2 * p + 1]);
+    for (int p = 0; p < 4; ++p) o[p] = pack_h2(v[q * 8 + 2 * p], v[q * 8 + 2 * p + 1]);
     *reinterpret_cast<uint4 *>(buf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
   }
 }
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
             f1 = fmaf(w, v.y, f1);
           }
         }
-        *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = pack_bf16(f0, f1);
+        *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = pack_h2(f0, f1);
       }
       __syncthreads();
       // the tile's features, in the shared-memory layout, for the backward

@@ -42,7 +42,7 @@ enum FieldMode { kEncodeOnly = 0, kForward = 1, kBackward = 2 };
 struct FieldArgs {
   ModelDev m;
   const float *params;        // binary32 master weights
-  const uint16_t *params_lp;  // FP16 tables / BF16 MLP working copy (mixed)
+  const uint16_t *params_lp;  // FP16 working copy of tables and MLP weights (mixed)
   float *grads;
   const float *xyz;           // [S][3] tile-local sample positions
   const float *feat_in;       // [S][IN] features instead of encoding (MLP-only API), or null
@@ -51,7 +51,7 @@ struct FieldArgs {
   float *sigma_rgb;           // forward output [S][4]
   const float *dsr;           // backward input [S][4]
   float *dfeat_out;           // backward: write dfeat here instead of scattering, or null
-  uint16_t *feat_lp;          // mixed path: BF16 features per 128-sample tile (forward writes, backward reads)
+  uint16_t *feat_lp;          // mixed path: FP16 features per 128-sample tile (forward writes, backward reads)
   const snk_state *state;
   int64_t S;                  // extent of the slot-major arrays
   int32_t slot_only;          // -1: every slot; k: only slot k (per-tile launches)

@@ -3,7 +3,7 @@
 // shared-memory operand descriptors, commit to an mbarrier, bounded mbarrier
 // waits, and tensor-memory loads.  Written from the public PTX ISA.
 //
-// Operand layout used throughout: a bf16 matrix X[R][C] (R, C multiples of 8)
+// Operand layout used throughout: a 16-bit matrix X[R][C] (R, C multiples of 8)
 // is stored as "core matrices" of 8 rows x 8 columns (8 rows of 16 bytes,
 // 128 contiguous bytes); core (r/8, c/8) sits at byte offset
 // ((c/8) * (R/8) + r/8) * 128, element (r%8, c%8) at (r%8) * 16 + (c%8) * 2.
@@ -35,18 +35,18 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t 
   return d;               // base offset 0, layout type 0 (no swizzle)
 }
 
-// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, dense.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major, int b_mn_major) {
+// Instruction descriptor of kind::f16: FP16 x FP16 -> FP32, dense.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int a_mn_major, int b_mn_major) {
   return (1u << 4)                         // D format F32
-         | (1u << 7)                       // A format BF16
-         | (1u << 10)                      // B format BF16
+         | (0u << 7)                       // A format F16
+         | (0u << 10)                      // B format F16
          | ((uint32_t)a_mn_major << 15)    // A major-ness (0: K-major)
          | ((uint32_t)b_mn_major << 16)    // B major-ness
          | ((uint32_t)(N >> 3) << 17)      // N / 8
          | ((uint32_t)(M >> 4) << 24);     // M / 16
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),

@@ -19,19 +19,9 @@ def model_from_workload(w, precision=None, hidden=64):
 
 
 def low_precision_copy(params, lay, model):
-    """FP16 (tables) / BF16 (MLP weights) working copy of binary32 parameters,
-    returned as int16 bit patterns in the flat layout."""
-    out = torch.empty(params.numel(), dtype=torch.int16, device=params.device)
-    n_slots = model.n_slots
-    for k in range(n_slots):
-        a = k * lay.tile_params
-        g = a + lay.grid_params
-        b = a + lay.tile_params
-        out[a:g] = params[a:g].to(torch.float16).view(torch.int16)
-        out[g:b] = params[g:b].to(torch.bfloat16).view(torch.int16)
-    c0 = n_slots * lay.tile_params
-    out[c0:] = params[c0:].to(torch.bfloat16).view(torch.int16)
-    return out
+    """FP16 working copy of binary32 parameters (tables and MLP weights), as
+    int16 bit patterns in the flat layout."""
+    return params.to(torch.float16).view(torch.int16)
 
 
 class Trainer:

@@ -1,8 +1,8 @@
-"""Mixed-precision path (FP16 tables, BF16 MLP on the tcgen05 tensor cores, FP32
+"""Mixed-precision path (FP16 tables, FP16 MLP on the tcgen05 tensor cores, FP32
 accumulation, loss scaling) against the FP64 oracle, through the C ABI.
 
-The oracle runs on the parameters the mixed model computes with: its working
-copy (tables rounded to FP16, MLP weights to BF16).  Tolerances: rendered RGB
+The oracle runs on the parameters the mixed model computes with: its FP16
+working copy.  Tolerances: rendered RGB
 and depth rel 2e-3 (floor 2e-3 x max), gradients 5e-3 norm-wise per tensor."""
 import numpy as np
 import pytest
@@ -32,11 +32,7 @@ def dev(a):
 
 def working_copy(params, cfg):
     """FP64 values of the mixed model's working copy of binary32 parameters."""
-    p = params.astype(np.float64).copy()
-    for a, b, mlp_a in OS.group_ranges(cfg):
-        p[a:mlp_a] = params[a:mlp_a].astype(np.float16).astype(np.float64)
-        p[mlp_a:b] = torch.from_numpy(params[mlp_a:b].copy()).to(torch.bfloat16).to(torch.float64).numpy()
-    return p
+    return params.astype(np.float16).astype(np.float64)
 
 
 def _trainer(ctx, case, seed=5, render=0):
@@ -76,10 +72,14 @@ def test_train_step_mixed_matches_oracle(ctx, name, n_rays, crop):
     e = RGB_REL_MIXED * 2 * max(1.0, np.abs(ref.rgb).max())
     assert abs(st["loss"] - ref.loss) <= 2 * np.sqrt(ref.loss) * e + 1e-7, (st["loss"], ref.loss)
     m = tr.m.cpu().numpy().astype(np.float64)
+    errs = {}
     for gi, (a, b, mlp_a) in enumerate(OS.group_ranges(case.cfg)):
         if mlp_a > a:
-            assert normwise(m[a:mlp_a], ref.m[a:mlp_a]) < GRAD_REL_MIXED, ("table", gi, normwise(m[a:mlp_a], ref.m[a:mlp_a]))
-        assert normwise(m[mlp_a:b], ref.m[mlp_a:b]) < GRAD_REL_MIXED, ("mlp", gi, normwise(m[mlp_a:b], ref.m[mlp_a:b]))
+            errs["table%d" % gi] = normwise(m[a:mlp_a], ref.m[a:mlp_a])
+        errs["mlp%d" % gi] = normwise(m[mlp_a:b], ref.m[mlp_a:b])
+    print("gradient errors (norm-wise):", errs)
+    assert max(errs.values()) < GRAD_REL_MIXED, errs
+    for gi, (a, b, mlp_a) in enumerate(OS.group_ranges(case.cfg)):
         # parameters with a clearly non-zero gradient move by the oracle's first Adam step
         pg = tr.params.cpu().numpy().astype(np.float64)[a:b]
         moved = ref.params[a:b] - wc[a:b]
@@ -109,9 +109,10 @@ def test_render_mixed_matches_oracle(ctx, name, n_rays):
 
 
 def test_mixed_training_reduces_the_loss_and_skips_overflow_steps(ctx):
-    """Twenty mixed steps on one tile: finite, decreasing loss.  A loss scale so
-    large that the scaled gradients overflow binary32 makes the step skip
-    (status bit 0), halve the scale and leave the weights unchanged."""
+    """Twenty mixed steps on a window: finite, decreasing loss.  A non-finite
+    value injected from the host into the gradient accumulator makes the next
+    step skip its update (status bit 0), halve the loss scale, leave the
+    weights unchanged and clear the accumulator."""
     case = make_case("tiny_window", n_rays=160, table_scale=1e-4)
     tr = _trainer(ctx, case)
     pix = dev(case.pix.view(np.int32))
@@ -122,10 +123,13 @@ def test_mixed_training_reduces_the_loss_and_skips_overflow_steps(ctx):
     assert ctx.sync_status(tr.state) == snk.SNK_OK
     assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
     before = tr.params.clone()
-    tr.state.view(torch.float32)[1] = 3.0e38
+    scale = tr.read_state()["loss_scale"]
+    steps = tr.steps.clone()
+    tr.grads[123] = float("nan")
     tr.train_step(pix)
     st = tr.read_state()
     assert st["status"] & snk.STATUS_OVERFLOW
-    assert st["loss_scale"] == pytest.approx(1.5e38, rel=1e-6)
-    assert torch.equal(tr.params, before)
+    assert st["loss_scale"] == pytest.approx(scale / 2, rel=1e-6)
+    assert torch.equal(tr.params, before) and torch.equal(tr.steps, steps)
+    assert torch.count_nonzero(tr.grads) == 0
     assert ctx.sync_status(tr.state) == snk.SNK_ERR_OVERFLOW
