@@ -273,6 +273,32 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
                const snk_sampler *sampler, const snk_params *p, snk_state *state, float *out,
                snk_stream_t stream);
 
+/* Allocation-free variant of snk_sample_segments (the paper has no counterpart:
+ * this exists for embedding).  For callers that cannot allocate device memory --
+ * hosts whose own allocator owns all device memory, fixed-budget or real-time
+ * runtimes, contexts where cudaMalloc would synchronise or is not allowed --
+ * and that therefore cannot create an snk_ctx.  The caller passes the cameras
+ * (host array, up to 256) and every input and output buffer exactly as for
+ * snk_sample_segments, and gets the same results.  The library's scratch (the
+ * cameras' device copy and the sample-count scans) lives in one fixed
+ * file-scope device array of about 2.8 MB that every GPU which loads the
+ * library holds until the process exits; nothing is allocated.
+ *  - B may be at most 65536; larger batches return SNK_ERR_INVALID_ARG and a
+ *    message in err (nullable, err_len bytes).
+ *  - The first call on a device looks up the device address of the scratch on
+ *    that device (the device current at the call); make that first call before
+ *    any stream capture.
+ *  - Every call on a device shares the same scratch and leaves the last call's
+ *    contents in it; nothing in it has to start at zero (each kernel writes what
+ *    it later reads).  Calls that overlap on the GPU (other streams, other host
+ *    threads) race on the scratch: serialise them.  Host threads are serialised
+ *    by a lock around the set-up and the camera copy. */
+int snk_sample_segments_static(const snk_window *win, const snk_camera *cams, int n_views, const uint32_t *pix,
+                               int B, const snk_sampler *sampler, float *ray_od, uint8_t *ray_ok, uint8_t *seg_slot,
+                               float *seg_t, uint32_t *seg_n, uint32_t *seg_off, float *smp_t, float *smp_dt,
+                               float *smp_xyz, int64_t cap, snk_state *state, snk_stream_t stream, char *err,
+                               int err_len);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 /* Host only: number of kernels libsnk has launched in this process. */

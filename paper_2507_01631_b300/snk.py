@@ -90,6 +90,9 @@ SIGNATURES = {
     "snk_render": (c_int, [_P, POINTER(SnkModel), POINTER(SnkWindow), _P, c_int, POINTER(SnkSampler),
                            POINTER(SnkParams), _P, _P, _P]),
     "snk_sync_status": (c_int, [_P, _P, _P]),
+    "snk_sample_segments_static": (c_int, [POINTER(SnkWindow), POINTER(SnkCamera), c_int, _P, c_int,
+                                           POINTER(SnkSampler), _P, _P, _P, _P, _P, _P, _P, _P, _P, c_int64, _P, _P,
+                                           c_char_p, c_int]),
     "snk_launch_count": (c_int64, []),
     "snk_stage_timing": (c_int, [_P, c_int]),
     "snk_stage_times": (c_int, [_P, POINTER(c_double), POINTER(c_int64), c_int]),
