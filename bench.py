@@ -40,8 +40,12 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="tile512_full")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--workload", default="window2x2_full")
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed"])
+    ap.add_argument("--graph", type=int, default=1, help="also time replays of the step captured as a CUDA graph")
+    ap.add_argument("--compare-fp32", type=int, default=1,
+                    help="also time the binary32 per-tile path on the same workload (mixed runs only)")
+    ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rays", type=int, default=256, help="rays per oracle sample (CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,11 +74,11 @@ def field_backward_work(w, precision):
     """Algorithmic FLOPs and bytes per sample of the fused field backward.
     FLOPs: recomputed MLP forward + input gradients + weight gradients (3 x the
     forward MACs x 2).  Bytes: binary32 path re-gathers the 8 corners of L
-    levels x F features (4 B each); the mixed path reads its stored FP16
+    levels x F features (4 B each); the mixed path reads its stored split-FP16 (hi, lo)
     features instead (2 B x L*F); both read xyz (12 B) and the upstream
     gradient (16 B) and scatter-add 8 corners x L x F binary32 (read + write)."""
     fl = 3 * mlp_flops_per_sample(w)
-    feat = w.L * 8 * w.F * 4 if precision == "fp32" else 2 * max(16, w.L * w.F)
+    feat = w.L * 8 * w.F * 4 if precision == "fp32" else 4 * max(16, w.L * w.F)
     scatter = w.L * 8 * w.F * 4 * 2
     return fl, feat + scatter + 12 + 16
 
@@ -85,7 +89,7 @@ def field_forward_work(w, precision):
     mixed path the FP16 features written for the backward."""
     if precision == "fp32":
         return mlp_flops_per_sample(w), w.L * 8 * w.F * 4 + 12 + 16
-    return mlp_flops_per_sample(w), w.L * 8 * w.F * 2 + 12 + 16 + 2 * max(16, w.L * w.F)
+    return mlp_flops_per_sample(w), w.L * 8 * w.F * 2 + 12 + 16 + 4 * max(16, w.L * w.F)
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -207,6 +211,50 @@ def run_reference(args, w):
 
 
 # ---- our arm ------------------------------------------------------------------------
+def time_steps(torch, tr, batches, steps, stream):
+    """Device time (ms) and samples of `steps` eager training steps."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    counts = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        tr.train_step(batches[i % len(batches)], stream=stream)
+        counts.append(tr.state[3:4].clone())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), int(sum(int(c.item()) & 0xFFFFFFFF for c in counts))
+
+
+def time_graph(torch, tr, batches, steps):
+    """Capture one training step into a CUDA graph (static pixel buffer) and time
+    `steps` replays, each preceded by a device copy of that step's batch."""
+    static_pix = torch.empty_like(batches[0])
+    static_pix.copy_(batches[0])
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        tr.train_step(static_pix, stream=side)  # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        tr.train_step(static_pix, stream=torch.cuda.current_stream())
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    counts = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        static_pix.copy_(batches[i % len(batches)], non_blocking=True)
+        g.replay()
+        counts.append(tr.state[3:4].clone())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), int(sum(int(c.item()) & 0xFFFFFFFF for c in counts))
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -293,6 +341,22 @@ def run_ours(args, w):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
+    extra = {}
+    if args.graph:
+        gms, gs = time_graph(torch, tr, batches, args.steps)
+        extra["graph_replay"] = {"value": gs / (gms / 1000.0), "unit": "samples/s", "ms_per_step": gms / args.steps,
+                                 "steps": args.steps}
+    if args.compare_fp32 and args.precision == "mixed":
+        m32 = model_from_workload(w, snk.SNK_FP32)
+        tr32 = Trainer(ctx, m32, snk.window_struct(w.window()), sampler, params)
+        tr32.train_step(batches[0], stream=stream)
+        fms, fs = time_steps(torch, tr32, batches, args.fp32_steps, stream)
+        rc32 = ctx.sync_status(tr32.state)
+        extra["fp32_per_tile"] = {"value": fs / (fms / 1000.0), "unit": "samples/s",
+                                  "ms_per_step": fms / args.fp32_steps, "steps": args.fp32_steps, "status": rc32,
+                                  "launches": "one field launch per tile and direction, eager"}
+        del tr32
+
     t_max = ms
     tot_samples = n_samples
     e2e_tot = e2e_samples
@@ -363,7 +427,7 @@ def run_ours(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16 (split) / f32 acc", "data": "synthetic",
         "config": {"workload": w.name, "precision": args.precision, "rays_per_step": w.n_rays,
                    "samples_per_step": n_samples / args.steps, "tiles": w.n_slots,
                    "grid": "L%d F%d T2^%d N%d-%d" % (w.L, w.F, w.log2_T, w.n_min, w.n_max),
@@ -376,6 +440,9 @@ def run_ours(args, w):
                 "d2h_bytes_per_step": int(snk.STATE_WORDS * 4)},
         "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
     }
+    line.update(extra)
+    if "fp32_per_tile" in extra and extra["fp32_per_tile"]["value"] > 0:
+        line["speedup_vs_fp32_per_tile"] = (n_samples / (ms / 1000.0)) / extra["fp32_per_tile"]["value"]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

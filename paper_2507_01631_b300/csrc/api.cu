@@ -27,7 +27,7 @@ struct snk_ctx {
   snk::RayBuffers rb{};
   float *sigma_rgb = nullptr;  // [cap_samples][4]
   float *dsr = nullptr;        // [cap_samples][4]
-  uint16_t *feat_lp = nullptr; // [cap_samples + 128][32] FP16 features of the mixed path
+  uint16_t *feat_lp = nullptr; // [cap_samples + 128][2][32] FP16 features (high, low parts), mixed path
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -238,7 +238,7 @@ size_t layout_ws(snk_ctx *ctx, char *base, int64_t B, int64_t S) {
   rb.smp_xyz = (float *)(base + carve(off, sizeof(float) * 3 * S));
   float *sr = (float *)(base + carve(off, sizeof(float) * 4 * S));
   float *dsr = (float *)(base + carve(off, sizeof(float) * 4 * S));
-  uint16_t *flp = (uint16_t *)(base + carve(off, sizeof(uint16_t) * 32 * (S + 128)));
+  uint16_t *flp = (uint16_t *)(base + carve(off, sizeof(uint16_t) * 64 * (S + 128)));
   if (base) {
     ctx->rb = rb;
     ctx->sigma_rgb = sr;

@@ -32,23 +32,42 @@ namespace {
 
 constexpr int TM = 128;  // samples per tile = MMA M
 constexpr int TT = 256;  // threads per CTA
+// Split FP16 operands (Markidis et al. 2018): every activation and delta x
+// that feeds an MMA is carried as hi = fp16(x) and lo = fp16((x - hi) * 2^11);
+// a layer runs two MMAs, hi * W and lo * W, into separate tensor-memory
+// accumulators and the epilogue adds D_hi + 2^-11 D_lo.  With the FP16
+// weights of the working copy exact, the layer then carries ~22 bits, so
+// the cancellation in 64-term dot products does not amplify 16-bit
+// rounding (the weight-gradient MMAs use the high parts only).
+constexpr float kLoScale = 2048.0f, kLoInv = 1.0f / 2048.0f;
+
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 template <int IN, bool BWD>
 struct L {
   static constexpr int INP = IN < 16 ? 16 : IN;  // layer-1 K padded to the MMA K step
-  // deltas first: the padded MN-major reads of dW run up to 32 KB past a delta
-  // buffer and must stay inside the allocation
+  // backward deltas (high parts) first: the padded MN-major reads of dW run up
+  // to 32 KB past a delta buffer and must stay inside the allocation
   static constexpr int DA = 0;                                 // [128 x 64]
   static constexpr int DB = BWD ? DA + TM * 64 * 2 : 0;        // [128 x 64]
   static constexpr int DG = BWD ? DB + TM * 64 * 2 : 0;        // [128 x 16]
   static constexpr int D3 = BWD ? DG + TM * 16 * 2 : 0;        // [128 x 16]
-  static constexpr int X0 = BWD ? D3 + TM * 16 * 2 : 0;        // [128 x INP]
+  // low parts (x 2^11): of the forward operands while the forward runs, then of the deltas
+  static constexpr int LO = BWD ? D3 + TM * 16 * 2 : 0;
+  static constexpr int XL0 = LO;                               // [128 x INP] features
+  static constexpr int XLA = XL0 + TM * INP * 2;               // [128 x 64] h1, then c1
+  static constexpr int XLB = XLA + TM * 64 * 2;                // [128 x 64] h2, then g, then c2
+  static constexpr int XL3 = XLB;
+  static constexpr int DAL = LO, DBL = LO + TM * 64 * 2, DGL = LO + 2 * TM * 64 * 2, D3L = DGL + TM * 16 * 2;
+  static constexpr int LO_END = LO + cmax(TM * INP * 2 + 2 * TM * 64 * 2, 2 * TM * 64 * 2 + 2 * TM * 16 * 2);
+  // high parts of the forward operands
+  static constexpr int X0 = LO_END;                            // [128 x INP]
   static constexpr int X1 = X0 + TM * INP * 2;                 // h1  [128 x 64]
   static constexpr int X2 = X1 + TM * 64 * 2;                  // h2
-  static constexpr int X3 = X2 + TM * 64 * 2;                  // g   [128 x 16]
-  static constexpr int X4 = BWD ? X3 + TM * 16 * 2 : X1;       // c1 (forward reuses h1's buffer)
-  static constexpr int X5 = BWD ? X4 + TM * 64 * 2 : X2;       // c2
-  static constexpr int W1 = BWD ? X5 + TM * 64 * 2 : X3 + TM * 16 * 2;  // [64 x INP]
+  static constexpr int X3 = BWD ? X2 + TM * 64 * 2 : X2;       // g [128 x 16] (forward: h2's buffer)
+  static constexpr int X4 = BWD ? X3 + TM * 16 * 2 : X1;       // c1 (forward: h1's buffer)
+  static constexpr int X5 = BWD ? X4 + TM * 64 * 2 : X2;       // c2 (forward: h2's buffer)
+  static constexpr int W1 = BWD ? X5 + TM * 64 * 2 : X2 + TM * 64 * 2;  // [64 x INP]
   static constexpr int W2 = W1 + 64 * INP * 2;                 // [64 x 64]
   static constexpr int W3 = W2 + 64 * 64 * 2;                  // [16 x 64]
   static constexpr int V1 = W3 + 16 * 64 * 2;                  // [64 x 16]
@@ -56,9 +75,10 @@ struct L {
   static constexpr int V3 = V2 + 64 * 64 * 2;                  // [16 x 64]
   static constexpr int END = V3 + 16 * 64 * 2;
   static constexpr int SMEM = END + 64;                        // + mbarrier and TMEM address
-  static constexpr uint32_t TCOLS = BWD ? 512 : 64;
-  // tensor-memory columns of the backward
+  static constexpr uint32_t TCOLS = BWD ? 512 : 128;
+  // tensor-memory columns: 0..63 accumulator of the high parts; C_DL the low parts
   static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
+  static constexpr uint32_t C_DL = BWD ? 448 : 64;
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
@@ -104,20 +124,24 @@ __device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, 
   }
 }
 
-// Epilogue of a [128 x 64] accumulator: this thread's row r and its 32-column half.
-// mode 0: ReLU -> out;  mode 1: out = v * (mask > 0)  (mask from a [128 x 64] activation buffer).
+// Epilogue of a [128 x 64] accumulator pair: this thread's row r and its 32-column half,
+// v = D_hi + 2^-11 D_lo.  mode 0: v = ReLU(v); mode 1: v *= (mask > 0) (mask from a
+// [128 x 64] activation buffer).  v is written as hi (out) and scaled lo (out_lo).
 template <int MODE>
-__device__ __forceinline__ void epi64(uint32_t taddr, uint8_t *out, const uint8_t *mask, int r, int ch) {
+__device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t *out, uint8_t *out_lo,
+                                      const uint8_t *mask, int r, int ch) {
   float v[32];
   {
-    float a[16], b[16];
+    float a[16], b[16], c[16], d[16];
     tc::ld16(taddr + ch * 32, a);
     tc::ld16(taddr + ch * 32 + 16, b);
+    tc::ld16(taddr_lo + ch * 32, c);
+    tc::ld16(taddr_lo + ch * 32 + 16, d);
     tc::wait_ld();
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      v[i] = a[i];
-      v[16 + i] = b[i];
+      v[i] = fmaf(c[i], kLoInv, a[i]);
+      v[16 + i] = fmaf(d[i], kLoInv, b[i]);
     }
   }
 #pragma unroll
@@ -127,7 +151,7 @@ __device__ __forceinline__ void epi64(uint32_t taddr, uint8_t *out, const uint8_
     uint4 m4 = make_uint4(0, 0, 0, 0);
     if (MODE == 1) m4 = *reinterpret_cast<const uint4 *>(mask + off);
     const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
-    uint32_t o[4];
+    uint32_t o[4], ol[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       float x0 = v[q * 8 + 2 * p], x1 = v[q * 8 + 2 * p + 1];
@@ -140,19 +164,38 @@ __device__ __forceinline__ void epi64(uint32_t taddr, uint8_t *out, const uint8_
         x1 = mk.y > 0.f ? x1 : 0.f;
       }
       o[p] = pack_h2(x0, x1);
+      const float2 h = unpack_h2(o[p]);
+      ol[p] = pack_h2((x0 - h.x) * kLoScale, (x1 - h.y) * kLoScale);
     }
     *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4 *>(out_lo + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
   }
 }
 
-// Store 16 floats as one FP16 row segment of a [128 x 16] buffer.
-__device__ __forceinline__ void store16(uint8_t *buf, int r, const float (&v)[16]) {
+// 16 columns of an accumulator pair, combined: v = D_hi + 2^-11 D_lo.
+__device__ __forceinline__ void ld16_pair(uint32_t taddr, uint32_t taddr_lo, float (&v)[16]) {
+  float lo[16];
+  tc::ld16(taddr, v);
+  tc::ld16(taddr_lo, lo);
+  tc::wait_ld();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = fmaf(lo[i], kLoInv, v[i]);
+}
+
+// Store 16 floats as one FP16 row segment of a [128 x 16] buffer (and, if buf_lo is
+// given, their scaled low parts).
+__device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, const float (&v)[16]) {
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    uint32_t o[4];
+    uint32_t o[4], ol[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) o[p] = pack_h2(v[q * 8 + 2 * p], v[q * 8 + 2 * p + 1]);
+    for (int p = 0; p < 4; ++p) {
+      o[p] = pack_h2(v[q * 8 + 2 * p], v[q * 8 + 2 * p + 1]);
+      const float2 h = unpack_h2(o[p]);
+      ol[p] = pack_h2((v[q * 8 + 2 * p] - h.x) * kLoScale, (v[q * 8 + 2 * p + 1] - h.y) * kLoScale);
+    }
     *reinterpret_cast<uint4 *>(buf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
+    if (buf_lo) *reinterpret_cast<uint4 *>(buf_lo + tc::core_off(r, q * 8, TM)) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
   }
 }
 
@@ -268,7 +311,7 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     const int64_t slot_end = (int64_t)st->slot_base[slot] + st->slot_count[slot];
     const int64_t idx = ts + r;
     const bool valid = idx < slot_end && idx < r1;
-    uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(TM * INP);
+    uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);  // [hi | lo] of the tile
 
     // ---- features ----
     if (!BWD) {
@@ -305,37 +348,48 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
             f1 = fmaf(w, v.y, f1);
           }
         }
-        *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = pack_h2(f0, f1);
+        const uint32_t hp = pack_h2(f0, f1);
+        const float2 hh = unpack_h2(hp);
+        *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = hp;
+        *reinterpret_cast<uint32_t *>(sm + Y::XL0 + tc::core_off(s, 2 * l, TM)) =
+            pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
       }
       __syncthreads();
-      // the tile's features, in the shared-memory layout, for the backward
-      for (int i = t; i < TM * INP * 2 / 16; i += TT)
+      // the tile's features (high and low parts), in the shared-memory layout, for the backward
+      for (int i = t; i < TM * INP * 2 / 16; i += TT) {
         reinterpret_cast<uint4 *>(ftile)[i] = reinterpret_cast<const uint4 *>(sm + Y::X0)[i];
+        reinterpret_cast<uint4 *>(ftile + TM * INP)[i] = reinterpret_cast<const uint4 *>(sm + Y::XL0)[i];
+      }
     } else {
-      for (int i = t; i < TM * INP * 2 / 16; i += TT)
+      for (int i = t; i < TM * INP * 2 / 16; i += TT) {
         reinterpret_cast<uint4 *>(sm + Y::X0)[i] = reinterpret_cast<const uint4 *>(ftile)[i];
+        reinterpret_cast<uint4 *>(sm + Y::XL0)[i] = reinterpret_cast<const uint4 *>(ftile + TM * INP)[i];
+      }
     }
     handoff();
 
     // ---- forward MLP ----
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X0, s0 + Y::W1, INP, 64);
+      mma_fwd(tmem + Y::C_DL, s0 + Y::XL0, s0 + Y::W1, INP, 64);
       tc::commit(mbar);
     }
     abort = !sync_mma();
     if (abort) break;
-    epi64<0>(trow, sm + Y::X1, nullptr, r, ch);
+    epi64<0>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch);
     handoff();
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X1, s0 + Y::W2, 64, 64);
+      mma_fwd(tmem + Y::C_DL, s0 + Y::XLA, s0 + Y::W2, 64, 64);
       tc::commit(mbar);
     }
     abort = !sync_mma();
     if (abort) break;
-    epi64<0>(trow, sm + Y::X2, nullptr, r, ch);
+    epi64<0>(trow, trow + Y::C_DL, sm + Y::X2, sm + Y::XLB, nullptr, r, ch);
     handoff();
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X2, s0 + Y::W3, 64, 16);
+      mma_fwd(tmem + Y::C_DL, s0 + Y::XLB, s0 + Y::W3, 64, 16);
       tc::commit(mbar);
     }
     abort = !sync_mma();
@@ -343,9 +397,8 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     float g[16];
     float rgb[3] = {0.f, 0.f, 0.f};
     if (ch == 0) {
-      tc::ld16(trow, g);
-      tc::wait_ld();
-      store16(sm + Y::X3, r, g);
+      ld16_pair(trow, trow + Y::C_DL, g);
+      store16(sm + Y::X3, sm + Y::XL3, r, g);
       if (!COL) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) rgb[k] = sigm(g[1 + k]);
@@ -355,30 +408,32 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     if (COL) {
       if (t == 0) {
         mma_fwd(tmem, s0 + Y::X3, s0 + Y::V1, 16, 64);
+        mma_fwd(tmem + Y::C_DL, s0 + Y::XL3, s0 + Y::V1, 16, 64);
         tc::commit(mbar);
       }
       abort = !sync_mma();
       if (abort) break;
-      epi64<0>(trow, sm + Y::X4, nullptr, r, ch);
+      epi64<0>(trow, trow + Y::C_DL, sm + Y::X4, sm + Y::XLA, nullptr, r, ch);
       handoff();
       if (t == 0) {
         mma_fwd(tmem, s0 + Y::X4, s0 + Y::V2, 64, 64);
+        mma_fwd(tmem + Y::C_DL, s0 + Y::XLA, s0 + Y::V2, 64, 64);
         tc::commit(mbar);
       }
       abort = !sync_mma();
       if (abort) break;
-      epi64<0>(trow, sm + Y::X5, nullptr, r, ch);
+      epi64<0>(trow, trow + Y::C_DL, sm + Y::X5, sm + Y::XLB, nullptr, r, ch);
       handoff();
       if (t == 0) {
         mma_fwd(tmem, s0 + Y::X5, s0 + Y::V3, 64, 16);
+        mma_fwd(tmem + Y::C_DL, s0 + Y::XLB, s0 + Y::V3, 64, 16);
         tc::commit(mbar);
       }
       abort = !sync_mma();
       if (abort) break;
       if (ch == 0) {
         float o[16];
-        tc::ld16(trow, o);
-        tc::wait_ld();
+        ld16_pair(trow, trow + Y::C_DL, o);
 #pragma unroll
         for (int k = 0; k < 3; ++k) rgb[k] = sigm(o[k]);
       }
@@ -406,13 +461,13 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
       if (COL) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) row[k] = d3[k];
-        store16(sm + Y::D3, r, row);
+        store16(sm + Y::D3, sm + Y::D3L, r, row);
         g[0] = dg0;  // keep dsigma's contribution to dg_0 for later
       } else {
         row[0] = dg0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) row[1 + k] = d3[k];
-        store16(sm + Y::DG, r, row);
+        store16(sm + Y::DG, sm + Y::DGL, r, row);
       }
     }
     handoff();
@@ -421,26 +476,29 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
       // dc2 = delta3 * V3, dV3 += delta3^T c2
       if (t == 0) {
         mma_dx(tmem, s0 + Y::D3, s0 + Y::V3, 16, 64);
+        mma_dx(tmem + Y::C_DL, s0 + Y::D3L, s0 + Y::V3, 16, 64);
         mma_dw(tmem + Y::C_V3, s0 + Y::D3, s0 + Y::X5, 64, acc);
         tc::commit(mbar);
       }
       abort = !sync_mma();
       if (abort) break;
-      epi64<1>(trow, sm + Y::DA, sm + Y::X5, r, ch);
+      epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X5, r, ch);
       handoff();
       // dc1 = delta_c2 * V2, dV2 += delta_c2^T c1
       if (t == 0) {
         mma_dx(tmem, s0 + Y::DA, s0 + Y::V2, 64, 64);
+        mma_dx(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::V2, 64, 64);
         mma_dw(tmem + Y::C_V2, s0 + Y::DA, s0 + Y::X4, 64, acc);
         tc::commit(mbar);
       }
       abort = !sync_mma();
       if (abort) break;
-      epi64<1>(trow, sm + Y::DB, sm + Y::X4, r, ch);
+      epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X4, r, ch);
       handoff();
       // dg = delta_c1 * V1 (+ dsigma term), dV1 += delta_c1^T g
       if (t == 0) {
         mma_dx(tmem, s0 + Y::DB, s0 + Y::V1, 64, 16);
+        mma_dx(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::V1, 64, 16);
         mma_dw(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, 16, acc);
         tc::commit(mbar);
       }
@@ -448,36 +506,43 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
       if (abort) break;
       if (ch == 0) {
         float dg[16];
+        float dgl[16];
         tc::ld16(trow, dg);
+        tc::ld16(trow + Y::C_DL, dgl);
         tc::wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dg[i] = fmaf(dgl[i], kLoInv, dg[i]);
         dg[0] += g[0];
-        store16(sm + Y::DG, r, dg);
+        store16(sm + Y::DG, sm + Y::DGL, r, dg);
       }
       handoff();
     }
     // dh2 = delta_g * W3 (masked by h2), dW3 += delta_g^T h2
     if (t == 0) {
       mma_dx(tmem, s0 + Y::DG, s0 + Y::W3, 16, 64);
+      mma_dx(tmem + Y::C_DL, s0 + Y::DGL, s0 + Y::W3, 16, 64);
       mma_dw(tmem + Y::C_W3, s0 + Y::DG, s0 + Y::X2, 64, acc);
       tc::commit(mbar);
     }
     abort = !sync_mma();
     if (abort) break;
-    epi64<1>(trow, sm + Y::DA, sm + Y::X2, r, ch);
+    epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X2, r, ch);
     handoff();
     // dh1 = delta_h2 * W2 (masked by h1), dW2 += delta_h2^T h1
     if (t == 0) {
       mma_dx(tmem, s0 + Y::DA, s0 + Y::W2, 64, 64);
+      mma_dx(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::W2, 64, 64);
       mma_dw(tmem + Y::C_W2, s0 + Y::DA, s0 + Y::X1, 64, acc);
       tc::commit(mbar);
     }
     abort = !sync_mma();
     if (abort) break;
-    epi64<1>(trow, sm + Y::DB, sm + Y::X1, r, ch);
+    epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X1, r, ch);
     handoff();
     // dfeat = delta_h1 * W1, dW1 += delta_h1^T feat
     if (t == 0) {
       mma_dx(tmem, s0 + Y::DB, s0 + Y::W1, 64, INP);
+      mma_dx(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::W1, 64, INP);
       mma_dw(tmem + Y::C_W1, s0 + Y::DB, s0 + Y::X0, INP, acc);
       tc::commit(mbar);
     }
@@ -487,9 +552,12 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     // ---- scatter dfeat into the table gradients ----
     const int c0 = ch * 16;
     if (c0 < IN) {
-      float df[16];
+      float df[16], dfl[16];
       tc::ld16(trow + c0, df);
+      tc::ld16(trow + Y::C_DL + c0, dfl);
       tc::wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) df[i] = fmaf(dfl[i], kLoInv, df[i]);
       if (valid) {
         float xyz[3];
 #pragma unroll
