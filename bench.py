@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--compare-fp32", type=int, default=1,
                     help="also time the binary32 per-tile path on the same workload (mixed runs only)")
     ap.add_argument("--fp32-steps", type=int, default=3)
+    ap.add_argument("--rays", type=int, default=0, help="override the workload's rays per step (profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rays", type=int, default=256, help="rays per oracle sample (CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -451,7 +452,7 @@ def run_ours(args, w):
 
 def main():
     args = parse()
-    w = W.get(args.workload)
+    w = W.get(args.workload, n_rays=args.rays) if args.rays > 0 else W.get(args.workload)
     if args.impl == "reference":
         run_reference(args, w)
     else:
