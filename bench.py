@@ -72,25 +72,34 @@ def mlp_flops_per_sample(w):
 
 
 def field_backward_work(w, precision):
-    """Algorithmic FLOPs and bytes per sample of the fused field backward.
+    """Algorithmic FLOPs and HBM bytes per sample of the fused field backward.
     FLOPs: recomputed MLP forward + input gradients + weight gradients (3 x the
-    forward MACs x 2).  Bytes: binary32 path re-gathers the 8 corners of L
-    levels x F features (4 B each); the mixed path reads its stored split-FP16 (hi, lo)
-    features instead (2 B x L*F); both read xyz (12 B) and the upstream
-    gradient (16 B) and scatter-add 8 corners x L x F binary32 (read + write)."""
+    forward MACs x 2).  HBM bytes: the binary32 path re-gathers the 8 corners of
+    L levels x F binary32 table entries (the tables and their gradients are
+    L2-resident, so the gather is counted once as a stream here only for the
+    binary32 baseline); the mixed path reads back its stored features (split
+    FP16, 4 B x L*F); both read xyz (12 B) and the upstream gradient (16 B).
+    The scatter-add of the table gradient (8 corners x L x F binary32 RMW) goes
+    to L2-resident memory and is reported as l2_red_bytes, not as HBM bytes."""
     fl = 3 * mlp_flops_per_sample(w)
     feat = w.L * 8 * w.F * 4 if precision == "fp32" else 4 * max(16, w.L * w.F)
-    scatter = w.L * 8 * w.F * 4 * 2
-    return fl, feat + scatter + 12 + 16
+    return fl, feat + 12 + 16
 
 
 def field_forward_work(w, precision):
-    """FLOPs: the MLP forward.  Bytes: the 8-corner gather of L x F table
-    entries (4 B binary32, 2 B FP16), xyz in, (sigma, rgb) out, and for the
-    mixed path the FP16 features written for the backward."""
+    """FLOPs: the MLP forward.  HBM bytes: xyz in (12 B), (sigma, rgb) out
+    (16 B) and, on the mixed path, the split-FP16 features written for the
+    backward (4 B x L*F); the table gather (8 corners x L x F) hits the
+    L2-resident tables and is reported as l2_gather_bytes."""
     if precision == "fp32":
-        return mlp_flops_per_sample(w), w.L * 8 * w.F * 4 + 12 + 16
-    return mlp_flops_per_sample(w), w.L * 8 * w.F * 2 + 12 + 16 + 4 * max(16, w.L * w.F)
+        return mlp_flops_per_sample(w), 12 + 16
+    return mlp_flops_per_sample(w), 12 + 16 + 4 * max(16, w.L * w.F)
+
+
+# DRAM bytes per sample of each kernel measured by ncu (--set full) on the 32768-ray case of the
+# 512 m tile (tile-local traffic grows with the samples processed); null once a kernel changes.
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward"): 174.3, ("mixed", "field_forward"): 149.0,
+                            ("fp32", "field_backward"): 736.6, ("fp32", "field_forward"): 42.5}
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -212,6 +221,18 @@ def run_reference(args, w):
 
 
 # ---- our arm ------------------------------------------------------------------------
+def reduce_over_ranks(maxes, sums, device):
+    """Whole-job figures of independent replicas: the max over ranks of each time,
+    the sum over ranks of each count (torch.distributed must be initialised)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(maxes, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(sums, device=device, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], [float(x) for x in c]
+
+
 def time_steps(torch, tr, batches, steps, stream):
     """Device time (ms) and samples of `steps` eager training steps."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -363,12 +384,7 @@ def run_ours(args, w):
     e2e_tot = e2e_samples
     e2e_max = e2e_ms
     if world > 1:
-        t = torch.tensor([ms, e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(t[0]), float(t[1])
-        c = torch.tensor([n_samples, e2e_samples], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        tot_samples, e2e_tot = float(c[0]), float(c[1])
+        (t_max, e2e_max), (tot_samples, e2e_tot) = reduce_over_ranks([ms, e2e_ms], [n_samples, e2e_samples], "cuda")
     value = tot_samples / (t_max / 1000.0)
     e2e_value = e2e_tot / (e2e_max / 1000.0)
 
@@ -392,11 +408,15 @@ def run_ours(args, w):
         else:
             fl, by = 0, 0
         sm_max = pk.get("sm_max_mhz", 2032.0)
+        dram = MEASURED_DRAM_PER_SAMPLE.get((args.precision, name))
+        traffic = dram * per_step_samples if dram is not None else None
+        l2 = {"l2_gather_bytes_per_sample": w.L * 8 * w.F * (4 if args.precision == "fp32" else 2),
+              "l2_red_bytes_per_sample": w.L * 8 * w.F * 4 * 2 if name == "field_backward" else 0}
         if args.precision == "fp32" and fl:
             peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
             achieved = fl * per_step_samples / per_launch_s / 1e12
             roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
                     "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived)" % sm_max}
         elif fl:
             gbs = by * per_step_samples / per_launch_s / 1e9
@@ -405,13 +425,15 @@ def run_ours(args, w):
                    "frac": gbs / pk["hbm_gbs"], "peak_source": "%s hbm_gbs" % pk["source"]}
             ten = {"bound": "tensor", "achieved": tfl, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
                    "frac": tfl / pk["bf16_tflops_sustained"],
-                   "peak_source": "%s bf16_tflops_sustained" % pk["source"]}
+                   "peak_source": "%s bf16_tflops_sustained (FP16 dense rate = BF16 rate)" % pk["source"]}
             main, other = (hbm, ten) if hbm["frac"] >= ten["frac"] else (ten, hbm)
             roof = dict(main)
-            roof.update({"kernel": name, "traffic": None, "other_bound": other})
+            roof.update({"kernel": name, "traffic": traffic, "other_bound": other})
         else:
             roof = {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None,
                     "traffic": None}
+        roof.update(l2)
+        roof["traffic_source"] = "ncu DRAM bytes per sample of the 32768-ray capture x samples per launch"
         roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
 
     cpu = None
