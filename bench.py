@@ -78,11 +78,17 @@ def field_backward_work(w, precision):
     L levels x F binary32 table entries (the tables and their gradients are
     L2-resident, so the gather is counted once as a stream here only for the
     binary32 baseline); the mixed path reads back its stored features (split
-    FP16, 4 B x L*F); both read xyz (12 B) and the upstream gradient (16 B).
+    FP16, 4 B x L*F; the E4M3 path its 1-byte codes); all read xyz (12 B) and
+    the upstream gradient (16 B).
     The scatter-add of the table gradient (8 corners x L x F binary32 RMW) goes
     to L2-resident memory and is reported as l2_red_bytes, not as HBM bytes."""
     fl = 3 * mlp_flops_per_sample(w)
-    feat = w.L * 8 * w.F * 4 if precision == "fp32" else 4 * max(16, w.L * w.F)
+    if precision == "fp32":
+        feat = w.L * 8 * w.F * 4
+    elif precision == "mixed_e4m3":
+        feat = max(16, w.L * w.F)       # the E4M3 codes, 1 B per feature
+    else:
+        feat = 4 * max(16, w.L * w.F)
     return fl, feat + 12 + 16
 
 
@@ -93,6 +99,10 @@ def field_forward_work(w, precision):
     L2-resident tables and is reported as l2_gather_bytes."""
     if precision == "fp32":
         return mlp_flops_per_sample(w), 12 + 16
+    if precision == "mixed_e4m3":
+        # gather pass: xyz in, binary32 features out; MLP pass: features in, codes and (sigma, rgb) out
+        IN = w.L * w.F
+        return mlp_flops_per_sample(w), 12 + 4 * IN + 4 * IN + max(16, IN) + 16
     return mlp_flops_per_sample(w), 12 + 16 + 4 * max(16, w.L * w.F)
 
 
@@ -160,7 +170,7 @@ def oracle_sample(w, cams, targets, params, seed, n_rays):
     from oracle import step as OS
     cfg = OS.ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, hidden=64,
                          geo_out=w.geo_out, colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots,
-                         K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max)
+                         K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max, first_layer=w.first_layer)
     pix = W.batch(w, cams, 1000 + seed, n_rays=n_rays)
     flat = params.astype(np.float64)
     n = len(flat)
@@ -293,7 +303,11 @@ def run_ours(args, w):
         B.build()
     if world > 1:
         dist.barrier()
-    precision = snk.SNK_MIXED if args.precision == "mixed" else snk.SNK_FP32
+    if args.precision == "mixed":
+        precision = snk.SNK_MIXED_E4M3 if w.first_layer == "e4m3" else snk.SNK_MIXED
+    else:
+        precision = snk.SNK_FP32
+    prec_key = {snk.SNK_FP32: "fp32", snk.SNK_MIXED: "mixed", snk.SNK_MIXED_E4M3: "mixed_e4m3"}[precision]
     model = model_from_workload(w, precision)
     cams, targets, params = make_inputs(w, snk.layout(model).grid_params)
     ctx = snk.Context(local)
@@ -402,13 +416,13 @@ def run_ours(args, w):
         per_launch_s = (sms / max(calls, 1)) / 1000.0
         per_step_samples = n_samples / max(args.steps, 1)
         if name == "field_backward":
-            fl, by = field_backward_work(w, args.precision)
+            fl, by = field_backward_work(w, prec_key)
         elif name == "field_forward":
-            fl, by = field_forward_work(w, args.precision)
+            fl, by = field_forward_work(w, prec_key)
         else:
             fl, by = 0, 0
         sm_max = pk.get("sm_max_mhz", 2032.0)
-        dram = MEASURED_DRAM_PER_SAMPLE.get((args.precision, name))
+        dram = MEASURED_DRAM_PER_SAMPLE.get((prec_key, name))
         traffic = dram * per_step_samples if dram is not None else None
         l2 = {"l2_gather_bytes_per_sample": w.L * 8 * w.F * (4 if args.precision == "fp32" else 2),
               "l2_red_bytes_per_sample": w.L * 8 * w.F * 4 * 2 if name == "field_backward" else 0}
@@ -450,8 +464,10 @@ def run_ours(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16 (split) / f32 acc", "data": "synthetic",
-        "config": {"workload": w.name, "precision": args.precision, "rays_per_step": w.n_rays,
+        "vs_baseline": None, "dtype": {"fp32": "f32", "mixed": "f16 (split) / f32 acc",
+                                       "mixed_e4m3": "e4m3 first layer, f16 (split) / f32 acc"}[prec_key],
+        "data": "synthetic",
+        "config": {"workload": w.name, "precision": prec_key, "rays_per_step": w.n_rays,
                    "samples_per_step": n_samples / args.steps, "tiles": w.n_slots,
                    "grid": "L%d F%d T2^%d N%d-%d" % (w.L, w.F, w.log2_T, w.n_min, w.n_max),
                    "views": "%d x %dpx %s" % (w.n_views, w.px, "rpc3" if w.cam_kind else "affine"),

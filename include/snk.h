@@ -62,8 +62,18 @@ enum {
 
 /* Camera kinds (Sec. 4.3 names the RPC model; affine is its linear case). */
 enum { SNK_CAM_AFFINE = 0, SNK_CAM_RPC3 = 1 };
-/* Precision of a model. */
-enum { SNK_FP32 = 0, SNK_MIXED = 1 };
+/* Precision of a model.
+ *  SNK_FP32:  binary32 tables, MLPs and gradients.
+ *  SNK_MIXED: FP16 working copy of every parameter, MLPs on the tensor cores
+ *             with FP32 accumulation, binary32 master weights, dynamic loss scale.
+ *  SNK_MIXED_E4M3: SNK_MIXED with the density MLP's first-layer input (the
+ *             encoded features) quantised to E4M3 (OCP FP8: 4 exponent bits,
+ *             3 mantissa bits, largest 448; round to nearest even, saturating).
+ *             One scale per slot and step, amax / 448 over the slot's features
+ *             of the current batch; the layer sees scale x value(code).  The
+ *             backward passes the feature gradient straight through the
+ *             quantiser. */
+enum { SNK_FP32 = 0, SNK_MIXED = 1, SNK_MIXED_E4M3 = 2 };
 
 /* One view: its localisation map (r, c, h) -> (x, y) and its resident crop.
  *  AFFINE: x = a0 + a1 c + a2 r + a3 h, y = b0 + b1 c + b2 r + b3 h.
@@ -112,7 +122,7 @@ typedef struct {
     int32_t colour;
     int32_t shared_colour;
     int32_t n_slots;
-    int32_t precision; /* SNK_FP32 or SNK_MIXED */
+    int32_t precision; /* SNK_FP32, SNK_MIXED or SNK_MIXED_E4M3 */
 } snk_model;
 
 /* Layout facts computed from a model on the host (no GPU needed). */
@@ -147,7 +157,7 @@ typedef struct {
 /* Trainable state, all device memory of n_params entries (snk_layout). */
 typedef struct {
     float *params;       /* binary32 master weights */
-    uint16_t *params_lp; /* SNK_MIXED: FP16 working copy of all parameters (tables and MLP weights); else NULL */
+    uint16_t *params_lp; /* SNK_MIXED*: FP16 working copy of all parameters (tables and MLP weights); else NULL */
     float *grads;        /* gradient accumulator; must be zero before a step, zeroed by the step */
     float *adam_m;
     float *adam_v;
@@ -272,6 +282,14 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
 int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
                const snk_sampler *sampler, const snk_params *p, snk_state *state, float *out,
                snk_stream_t stream);
+
+/* E4M3 quantiser of the SNK_MIXED_E4M3 first layer: codes[i] = E4M3(x[i] /
+ * scale) for n binary32 device values (the division rounded to nearest, then
+ * rounded to nearest even on the E4M3 grid, magnitudes beyond 448 saturating).
+ * Device buffers owned by the caller; scale must be positive and finite, else
+ * SNK_ERR_INVALID_ARG.  The same conversion the training step applies with the
+ * per-slot scale amax / 448. */
+int snk_quantize_e4m3(snk_ctx *ctx, const float *x, int64_t n, float scale, uint8_t *codes, snk_stream_t stream);
 
 /* Allocation-free variant of snk_sample_segments (the paper has no counterpart:
  * this exists for embedding).  For callers that cannot allocate device memory --

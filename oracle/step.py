@@ -17,7 +17,7 @@ Flat parameter layout (also the library's):
 from dataclasses import dataclass, field
 import numpy as np
 
-from . import adam, camera, hashgrid, mlp, render, sampler
+from . import adam, camera, hashgrid, mlp, quant, render, sampler
 
 
 @dataclass
@@ -35,6 +35,7 @@ class ModelConfig:
     K_ray: int = 64
     K_min: int = 64
     K_max: int = 64
+    first_layer: str = "f16"    # "e4m3": the density MLP's input is quantised (quant.py)
 
     def grid(self):
         return hashgrid.layout(self.L, self.F, self.log2_T, self.n_min, self.n_max)
@@ -147,12 +148,21 @@ def field_forward(cfg, flat, smp):
             continue
         table, geo = tiles[s]
         feat = hashgrid.encode(smp.xyz[m], table, lay)
+        scale = None
+        if cfg.first_layer == "e4m3":
+            # per-tensor scale of this slot's first-layer input from the current batch; the codes
+            # are decided in binary32 (the kernel's precision), the MLP sees scale x value(code)
+            # and its backward passes dfeat straight through the quantiser
+            f32 = quant.encode_binary32(smp.xyz[m], table, lay)
+            scale = quant.slot_scale_binary32(f32)
+            feat = quant.quantise_binary32(f32, scale)
         col = None
         if cfg.colour:
             col = cols[0] if cfg.shared_colour else cols[s]
         sg, rg, acts = mlp.forward(feat, geo, col)
         sigma[m] = sg
         rgb[m] = rg
+        acts["scale"] = scale
         saved[s] = (m, feat, acts, col)
     return sigma, rgb, saved
 

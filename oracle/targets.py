@@ -1,24 +1,38 @@
 """Target images of the synthetic scenes (oracle, FP64).  Test infrastructure only.
 
 The paper trains on real WorldView-3 images (Sec. 5.1), not available here.
-Stand-in: a heightfield surface z = h(x, y) (synth.heightfield) seen by the
-synthetic cameras.  The colour of a pixel is the Lambertian shading of the
+Stand-in: a heightfield surface z = h(x, y) seen by the synthetic cameras,
+either a sum of sinusoids (synth.heightfield) or raster blocks
+(synth.blocks).  The colour of a pixel is the Lambertian shading of the
 first surface point its ray hits:
     colour = albedo(x, y) * (0.2 + 0.8 max(0, n . s))
-with n the unit normal (-dh/dx, -dh/dy, 1)/|.|, s the sun direction and
-albedo the bilinear interpolation of the 32 x 32 colour noise over the scene's
-xy box.  The hit is found by marching the ray from z_max in steps of at most
+with s the sun direction, albedo the bilinear interpolation of the 32 x 32
+colour noise over the scene's xy box, and n the unit normal: for the
+sinusoids (-dh/dx, -dh/dy, 1)/|.|; for the blocks (0, 0, 1) on a roof, and on
+a wall (the hit lies below the roof of the cell entered, coming from another
+cell) the horizontal axis across which the ray entered, pointing back out
+(the x axis when both changed).  The hit is found by marching the ray from z_max in steps of at most
 `step` metres of height and refining the first sign change of
 z(t) - h(x(t), y(t)) by bisection to 1e-9 m.  Rays that reach z_min or leave
 the box without a hit get colour 0.
 """
 import numpy as np
 
-from synth import pack_pixel
+from synth import Blocks, pack_pixel
 from .camera import rays_fp64
 
 
+def _cell(hf, x, y):
+    n = hf.H.shape[0]
+    j = np.clip(np.floor((x - hf.lo[0]) / (hf.hi[0] - hf.lo[0]) * n), 0, n - 1).astype(np.int64)
+    i = np.clip(np.floor((y - hf.lo[1]) / (hf.hi[1] - hf.lo[1]) * n), 0, n - 1).astype(np.int64)
+    return i, j
+
+
 def height(hf, x, y):
+    if isinstance(hf, Blocks):
+        i, j = _cell(hf, x, y)
+        return hf.H[i, j]
     z = np.full_like(x, hf.z_base)
     for a, k, p in zip(hf.amp, hf.k, hf.phase):
         z = z + a * np.sin(2 * np.pi * (k[0] * x + k[1] * y) + p)
@@ -33,6 +47,27 @@ def height_grad(hf, x, y):
         gx = gx + c * k[0]
         gy = gy + c * k[1]
     return gx, gy
+
+
+def normals(hf, p_out, p_in):
+    """Unit normals at hits bracketed by p_out (above the surface) and p_in
+    (below it, the shaded point)."""
+    if isinstance(hf, Blocks):
+        io, jo = _cell(hf, p_out[:, 0], p_out[:, 1])
+        ii, ji = _cell(hf, p_in[:, 0], p_in[:, 1])
+        wall = ((io != ii) | (jo != ji)) & (hf.H[ii, ji] - p_in[:, 2] > 1e-6)
+        nrm = np.zeros_like(p_in)
+        nrm[:, 2] = 1.0
+        wx = wall & (jo != ji)
+        wy = wall & (jo == ji)
+        nrm[wx] = 0.0
+        nrm[wx, 0] = np.sign(p_out[wx, 0] - p_in[wx, 0])
+        nrm[wy] = 0.0
+        nrm[wy, 1] = np.sign(p_out[wy, 1] - p_in[wy, 1])
+        return nrm
+    gx, gy = height_grad(hf, p_in[:, 0], p_in[:, 1])
+    nrm = np.stack([-gx, -gy, np.ones_like(gx)], 1)
+    return nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
 
 
 def albedo(hf, x, y):
@@ -88,9 +123,7 @@ def shade_rays(hf, top, d, step=1.0):
     if lo.size:
         p = tp + hi[:, None] * dd
         inside = ((p[:, 0] >= hf.lo[0]) & (p[:, 0] <= hf.hi[0]) & (p[:, 1] >= hf.lo[1]) & (p[:, 1] <= hf.hi[1]))
-        gx, gy = height_grad(hf, p[:, 0], p[:, 1])
-        nrm = np.stack([-gx, -gy, np.ones_like(gx)], 1)
-        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        nrm = normals(hf, tp + lo[:, None] * dd, p)
         lam = 0.2 + 0.8 * np.maximum(0.0, nrm @ hf.sun)
         col = albedo(hf, p[:, 0], p[:, 1]) * lam[:, None]
         out[np.flatnonzero(found)] = np.where(inside[:, None], col, 0.0)

@@ -27,7 +27,10 @@ struct snk_ctx {
   snk::RayBuffers rb{};
   float *sigma_rgb = nullptr;  // [cap_samples][4]
   float *dsr = nullptr;        // [cap_samples][4]
-  uint16_t *feat_lp = nullptr; // [cap_samples + 128][2][32] FP16 features (high, low parts), mixed path
+  uint16_t *feat_lp = nullptr; // [cap_samples + 128][2][32] FP16 features (high, low parts), mixed path;
+                               // the E4M3 path uses the same bytes as [cap_samples + 128][32] binary32 features
+  uint8_t *codes = nullptr;    // [cap_samples + 128][32] E4M3 first-layer codes
+  uint32_t *amax = nullptr;    // [4] per-slot max |feature| (binary32 bits), E4M3 path
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -104,7 +107,8 @@ int layout_of(const snk_model *m, snk_layout *o, char *msg, size_t msg_len) {
   if (m->geo_out != (m->colour ? 16 : 4)) return bad("geo_out must be 16 with a colour MLP, 4 without");
   if (m->shared_colour != 0 && m->shared_colour != 1) return bad("shared_colour must be 0 or 1");
   if (m->n_slots < 1 || m->n_slots > kMaxSlots) return bad("n_slots must be in 1..4");
-  if (m->precision != SNK_FP32 && m->precision != SNK_MIXED) return bad("precision must be SNK_FP32 or SNK_MIXED");
+  if (m->precision != SNK_FP32 && m->precision != SNK_MIXED && m->precision != SNK_MIXED_E4M3)
+    return bad("precision must be SNK_FP32, SNK_MIXED or SNK_MIXED_E4M3");
   memset(o, 0, sizeof(*o));
   const int64_t T = (int64_t)1 << m->log2_T;
   const double b = m->L > 1 ? std::exp((std::log((double)m->n_max) - std::log((double)m->n_min)) / (m->L - 1)) : 1.0;
@@ -148,7 +152,8 @@ ModelDev model_dev(const snk_model *m, const snk_layout &lay) {
   d.colour = m->colour;
   d.shared_colour = m->shared_colour;
   d.n_slots = m->n_slots;
-  d.mixed = m->precision == SNK_MIXED;
+  d.mixed = m->precision != SNK_FP32;
+  d.e4m3 = m->precision == SNK_MIXED_E4M3;
   d.tile_params = lay.tile_params;
   d.grid_params = lay.grid_params;
   d.colour_params = lay.colour_params;
@@ -239,11 +244,15 @@ size_t layout_ws(snk_ctx *ctx, char *base, int64_t B, int64_t S) {
   float *sr = (float *)(base + carve(off, sizeof(float) * 4 * S));
   float *dsr = (float *)(base + carve(off, sizeof(float) * 4 * S));
   uint16_t *flp = (uint16_t *)(base + carve(off, sizeof(uint16_t) * 64 * (S + 128)));
+  uint8_t *codes = (uint8_t *)(base + carve(off, (size_t)32 * (S + 128)));
+  uint32_t *amax = (uint32_t *)(base + carve(off, sizeof(uint32_t) * kMaxSlots));
   if (base) {
     ctx->rb = rb;
     ctx->sigma_rgb = sr;
     ctx->dsr = dsr;
     ctx->feat_lp = flp;
+    ctx->codes = codes;
+    ctx->amax = amax;
   }
   return off;
 }
@@ -287,7 +296,7 @@ int prepare(snk_ctx *ctx, const snk_model *model, snk_layout *lay, ModelDev *md)
 
 int check_params(snk_ctx *ctx, const snk_model *model, const snk_params *p, bool train) {
   if (!p || !p->params) return fail(ctx, SNK_ERR_INVALID_ARG, "params is NULL");
-  if (model->precision == SNK_MIXED && !p->params_lp)
+  if (model->precision != SNK_FP32 && !p->params_lp)
     return fail(ctx, SNK_ERR_INVALID_ARG, "mixed precision needs the params_lp working copy");
   if (train && (!p->grads || !p->adam_m || !p->adam_v || !p->adam_step))
     return fail(ctx, SNK_ERR_INVALID_ARG, "training needs grads, adam_m, adam_v and adam_step");
@@ -564,11 +573,19 @@ static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, c
   fa.sigma_rgb = ctx->sigma_rgb;
   fa.dsr = ctx->dsr;
   fa.feat_lp = ctx->feat_lp;
+  fa.feat32 = reinterpret_cast<float *>(ctx->feat_lp);
+  fa.codes = ctx->codes;
+  fa.amax = ctx->amax;
   fa.state = state;
   fa.S = ctx->cap_samples;
   fa.mode = mode;
-  if (model->precision == SNK_MIXED) {
+  if (model->precision != SNK_FP32) {
     fa.slot_only = -1;
+    if (md.e4m3 && mode == kForward) {
+      // the per-slot scales need every feature of the batch first
+      SNK_CK(ctx, cudaMemsetAsync(ctx->amax, 0, sizeof(uint32_t) * kMaxSlots, st));
+      SNK_CK(ctx, launch_gather_amax(fa, ctx->sm_count, st));
+    }
     SNK_CK(ctx, launch_field_tc(fa, ctx->sm_count, st));
     return SNK_OK;
   }
@@ -655,7 +672,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   aa.eps = adam->eps;
   aa.l2 = adam->l2_mlp;
   aa.state = state;
-  aa.mixed = model->precision == SNK_MIXED;
+  aa.mixed = model->precision != SNK_FP32;
   {
     StageMark m(ctx, 4, st);
     SNK_CK(ctx, launch_adam(aa, ctx->sm_count, st));
@@ -702,6 +719,16 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
     StageMark m(ctx, 2, st);
     SNK_CK(ctx, launch_composite(ca, st));
   }
+  return SNK_OK;
+}
+
+int snk_quantize_e4m3(snk_ctx *ctx, const float *x, int64_t n, float scale, uint8_t *codes, snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!x || !codes)))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_quantize_e4m3: NULL buffer or negative n");
+  if (!(scale > 0.0f) || !std::isfinite(scale))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_quantize_e4m3: scale must be positive and finite");
+  SNK_CK(ctx, launch_quantize_e4m3(x, n, scale, codes, (cudaStream_t)stream));
   return SNK_OK;
 }
 

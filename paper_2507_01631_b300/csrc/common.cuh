@@ -123,6 +123,27 @@ __device__ __forceinline__ int slot_of(const snk_state *st, int64_t s) {
 
 __device__ __forceinline__ void set_status(snk_state *st, uint32_t bit) { atomicOr(&st->status, bit); }
 
+// ---- E4M3 (OCP 8-bit float: sign, 4 exponent bits with bias 7, 3 mantissa bits,
+// largest finite 448, no infinities) -----------------------------------------
+// Two binary32 values to an E4M3 pair (lo in the low byte): round to nearest
+// even, magnitudes beyond 448 saturate to 448.
+__device__ __forceinline__ uint16_t e4m3x2_from_f32(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// An E4M3 pair as an FP16 pair (exact: every E4M3 value is an FP16 value).
+__device__ __forceinline__ uint32_t f16x2_from_e4m3x2(uint16_t c) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"(c));
+  return r;
+}
+// Per-slot scale of the E4M3 first-layer input: amax / 448 (1 for an all-zero slot).
+__device__ __forceinline__ float e4m3_scale(uint32_t amax_bits) {
+  const float amax = __uint_as_float(amax_bits);
+  return amax > 0.f ? fdiv(amax, 448.0f) : 1.0f;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -127,21 +127,25 @@ __device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, 
 // Epilogue of a [128 x 64] accumulator pair: this thread's row r and its 32-column half,
 // v = D_hi + 2^-11 D_lo.  mode 0: v = ReLU(v); mode 1: v *= (mask > 0) (mask from a
 // [128 x 64] activation buffer).  v is written as hi (out) and scaled lo (out_lo).
-template <int MODE>
+// LO = false: the layer had no low-part MMA (E4M3 first layer, whose input is exact in
+// FP16); scale multiplies the sum (the E4M3 input's per-slot scale, else 1).
+template <int MODE, bool LO = true>
 __device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t *out, uint8_t *out_lo,
-                                      const uint8_t *mask, int r, int ch) {
+                                      const uint8_t *mask, int r, int ch, float scale = 1.0f) {
   float v[32];
   {
     float a[16], b[16], c[16], d[16];
     tc::ld16(taddr + ch * 32, a);
     tc::ld16(taddr + ch * 32 + 16, b);
-    tc::ld16(taddr_lo + ch * 32, c);
-    tc::ld16(taddr_lo + ch * 32 + 16, d);
+    if (LO) {
+      tc::ld16(taddr_lo + ch * 32, c);
+      tc::ld16(taddr_lo + ch * 32 + 16, d);
+    }
     tc::wait_ld();
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      v[i] = fmaf(c[i], kLoInv, a[i]);
-      v[16 + i] = fmaf(d[i], kLoInv, b[i]);
+      v[i] = LO ? fmaf(c[i], kLoInv, a[i]) : a[i] * scale;
+      v[16 + i] = LO ? fmaf(d[i], kLoInv, b[i]) : b[i] * scale;
     }
   }
 #pragma unroll
@@ -201,7 +205,7 @@ __device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, co
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
-template <int IN, int G, bool COL, bool BWD>
+template <int IN, int G, bool COL, bool BWD, bool Q8>
 __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
   using Y = L<IN, BWD>;
   constexpr int INP = Y::INP;
@@ -271,9 +275,12 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
                        {Y::C_W3, 64, G, 64, gs + m.w3},   {Y::C_V1, 16, 64, G, gc + m.v1},
                        {Y::C_V2, 64, 64, 64, gc + m.v2},  {Y::C_V3, 64, 3, 64, gc + m.v3}};
     const int nreg = COL ? 6 : 3;
+    // E4M3 first layer: the dW1 MMAs read the codes' values; the layer's input is scale x value
+    const float s1 = Q8 ? e4m3_scale(a.amax[k]) : 1.0f;
     for (int q = 0; q < nreg; ++q) {
       const R &g = regs[q];
       if ((warp & 3) >= 2) continue;  // rows >= 64 are padding
+      const float sc = q == 0 ? s1 : 1.0f;
       for (int c0 = ch * 16; c0 < g.ncol; c0 += 32) {
         float v[16];
         tc::ld16(trow + g.col + c0, v);
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
         if (r < g.out) {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            if (c0 + i < g.in && v[i] != 0.f) atomicAdd(g.dst + (int64_t)r * g.in + c0 + i, v[i]);
+            if (c0 + i < g.in && v[i] != 0.f) atomicAdd(g.dst + (int64_t)r * g.in + c0 + i, v[i] * sc);
         }
       }
     }
@@ -314,7 +321,55 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);  // [hi | lo] of the tile
 
     // ---- features ----
-    if (!BWD) {
+    const float s1 = Q8 ? e4m3_scale(a.amax[slot]) : 1.0f;  // E4M3 first layer: the slot's scale
+    if (Q8) {
+      // forward: quantise the binary32 features of the gather pass and keep the codes for the
+      // backward; backward: reload the codes.  Both widen them to FP16 (exact) into X0.
+      const int s = t & (TM - 1), half = t >> 7;
+      const int64_t sidx = ts + s;
+      const bool sval = sidx < slot_end && sidx < r1;
+      if (16 * half < INP) {
+        uint8_t *cp = a.codes + sidx * INP + 16 * half;  // this thread's 16 codes
+        uint32_t cw[4];
+        if (!BWD) {
+          float f[16];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sval && 16 * half + 4 * j < IN)
+              v = *reinterpret_cast<const float4 *>(a.feat32 + sidx * IN + 16 * half + 4 * j);
+            f[4 * j] = v.x;
+            f[4 * j + 1] = v.y;
+            f[4 * j + 2] = v.z;
+            f[4 * j + 3] = v.w;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint16_t c01 = e4m3x2_from_f32(fdiv(f[4 * j], s1), fdiv(f[4 * j + 1], s1));
+            const uint16_t c23 = e4m3x2_from_f32(fdiv(f[4 * j + 2], s1), fdiv(f[4 * j + 3], s1));
+            cw[j] = (uint32_t)c01 | ((uint32_t)c23 << 16);
+          }
+          *reinterpret_cast<uint4 *>(cp) = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+        } else {
+          const uint4 v = *reinterpret_cast<const uint4 *>(cp);
+          cw[0] = v.x;
+          cw[1] = v.y;
+          cw[2] = v.z;
+          cw[3] = v.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          uint32_t h[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const uint32_t w = cw[2 * q + (p >> 1)];
+            h[p] = f16x2_from_e4m3x2((uint16_t)((p & 1) ? (w >> 16) : (w & 0xffffu)));
+          }
+          *reinterpret_cast<uint4 *>(sm + Y::X0 + tc::core_off(s, 16 * half + 8 * q, TM)) =
+              make_uint4(h[0], h[1], h[2], h[3]);
+        }
+      }
+    } else if (!BWD) {
       const int s = t & (TM - 1), half = t >> 7;
       const int64_t sidx = ts + s;
       const bool sval = sidx < slot_end && sidx < r1;
@@ -371,12 +426,15 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     // ---- forward MLP ----
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X0, s0 + Y::W1, INP, 64);
-      mma_fwd(tmem + Y::C_DL, s0 + Y::XL0, s0 + Y::W1, INP, 64);
+      if (!Q8) mma_fwd(tmem + Y::C_DL, s0 + Y::XL0, s0 + Y::W1, INP, 64);
       tc::commit(mbar);
     }
     abort = !sync_mma();
     if (abort) break;
-    epi64<0>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch);
+    if (Q8)
+      epi64<0, false>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch, s1);
+    else
+      epi64<0>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch);
     handoff();
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X1, s0 + Y::W2, 64, 64);
@@ -601,10 +659,10 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
   if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
 }
 
-template <int IN, int G, bool COL, bool BWD>
+template <int IN, int G, bool COL, bool BWD, bool Q8>
 cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
   using Y = L<IN, BWD>;
-  auto k = k_field_tc<IN, G, COL, BWD>;
+  auto k = k_field_tc<IN, G, COL, BWD, Q8>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
@@ -621,22 +679,29 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int IN, int G, bool COL>
+template <int IN, int G, bool COL, bool Q8>
 cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st) {
-  if (a.mode == kBackward) return launch_t<IN, G, COL, true>(a, sm_count, st);
-  return launch_t<IN, G, COL, false>(a, sm_count, st);
+  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8>(a, sm_count, st);
+  return launch_t<IN, G, COL, false, Q8>(a, sm_count, st);
+}
+
+template <int IN, int G, bool COL>
+cudaError_t launch_q(const FieldArgs &a, int sm_count, cudaStream_t st) {
+  if (a.m.e4m3) return launch_mode<IN, G, COL, true>(a, sm_count, st);
+  return launch_mode<IN, G, COL, false>(a, sm_count, st);
 }
 
 template <int IN>
 cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st) {
-  if (a.m.colour) return launch_mode<IN, 16, true>(a, sm_count, st);
-  return launch_mode<IN, 4, false>(a, sm_count, st);
+  if (a.m.colour) return launch_q<IN, 16, true>(a, sm_count, st);
+  return launch_q<IN, 4, false>(a, sm_count, st);
 }
 
 }  // namespace
 
 cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st) {
   if (a.mode == kEncodeOnly || a.feat_lp == nullptr || a.params_lp == nullptr) return cudaErrorInvalidValue;
+  if (a.m.e4m3 && (a.feat32 == nullptr || a.codes == nullptr || a.amax == nullptr)) return cudaErrorInvalidValue;
   switch (a.m.in_dim) {
     case 8: return launch_in<8>(a, sm_count, st);
     case 16: return launch_in<16>(a, sm_count, st);

@@ -32,6 +32,7 @@ cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinP
 struct ModelDev {
   GridParams grid;
   int32_t in_dim, geo_out, colour, shared_colour, n_slots, mixed;
+  int32_t e4m3;  // mixed path with an E4M3 first-layer input (one scale per slot and step)
   int64_t tile_params, grid_params, colour_params, colour_base;
   int64_t w1, w2, w3;  // offsets of the density-MLP matrices inside a slot block
   int64_t v1, v2, v3;  // offsets of the colour-MLP matrices inside a colour block
@@ -52,6 +53,9 @@ struct FieldArgs {
   const float *dsr;           // backward input [S][4]
   float *dfeat_out;           // backward: write dfeat here instead of scattering, or null
   uint16_t *feat_lp;          // mixed path: FP16 features per 128-sample tile (forward writes, backward reads)
+  float *feat32;              // E4M3 path: [S][IN] binary32 features (gather writes, forward reads)
+  uint8_t *codes;             // E4M3 path: [S][IN] first-layer codes (forward writes, backward reads)
+  uint32_t *amax;             // E4M3 path: per slot, bits of max |feature| of the step (>= 0 floats)
   const snk_state *state;
   int64_t S;                  // extent of the slot-major arrays
   int32_t slot_only;          // -1: every slot; k: only slot k (per-tile launches)
@@ -61,6 +65,11 @@ cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st)
 cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st);
 // Scatter-add feat_in (read as dfeat [S][L*F]) into the table gradients.
 cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st);
+// E4M3 path, first pass: binary32 features from the FP16 tables into feat32 and
+// the per-slot max |feature| into amax (which must be zero before the launch).
+cudaError_t launch_gather_amax(const FieldArgs &a, int sm_count, cudaStream_t st);
+// codes[i] = E4M3(x[i] / scale), the conversion the E4M3 path uses.
+cudaError_t launch_quantize_e4m3(const float *x, int64_t n, float scale, uint8_t *codes, cudaStream_t st);
 
 struct CompositeArgs {
   const float *sigma_rgb;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libsnk.so")
 
 SNK_OK, SNK_ERR_INVALID_ARG, SNK_ERR_CUDA, SNK_ERR_OOM, SNK_ERR_TIMEOUT, SNK_ERR_DEVICE_CHECK, SNK_ERR_OVERFLOW = range(7)
 SNK_CAM_AFFINE, SNK_CAM_RPC3 = 0, 1
-SNK_FP32, SNK_MIXED = 0, 1
+SNK_FP32, SNK_MIXED, SNK_MIXED_E4M3 = 0, 1, 2
 STATUS_OVERFLOW, STATUS_CHECK, STATUS_TIMEOUT = 1, 2, 4
 
 
@@ -90,6 +90,7 @@ SIGNATURES = {
     "snk_render": (c_int, [_P, POINTER(SnkModel), POINTER(SnkWindow), _P, c_int, POINTER(SnkSampler),
                            POINTER(SnkParams), _P, _P, _P]),
     "snk_sync_status": (c_int, [_P, _P, _P]),
+    "snk_quantize_e4m3": (c_int, [_P, _P, c_int64, c_float, _P, _P]),
     "snk_sample_segments_static": (c_int, [POINTER(SnkWindow), POINTER(SnkCamera), c_int, _P, c_int,
                                            POINTER(SnkSampler), _P, _P, _P, _P, _P, _P, _P, _P, _P, c_int64, _P, _P,
                                            c_char_p, c_int]),

@@ -13,7 +13,11 @@ STATE_FIELDS = {"loss": (0, "f"), "loss_scale": (1, "f"), "n_accepted": (2, "u")
 
 
 def model_from_workload(w, precision=None, hidden=64):
-    prec = precision if precision is not None else (snk.SNK_MIXED if w.mixed else snk.SNK_FP32)
+    if precision is None:
+        precision = snk.SNK_FP32
+        if w.mixed:
+            precision = snk.SNK_MIXED_E4M3 if getattr(w, "first_layer", "f16") == "e4m3" else snk.SNK_MIXED
+    prec = precision
     return snk.model_struct(w.L, w.F, w.log2_T, w.n_min, w.n_max, w.geo_out, w.colour, w.shared_colour,
                             w.n_slots, prec, hidden)
 
@@ -38,7 +42,7 @@ class Trainer:
         p = torch.as_tensor(np.asarray(init_params, np.float32)).to(device)
         assert p.numel() == n, (p.numel(), n)
         self.params = p.contiguous()
-        self.mixed = model.precision == snk.SNK_MIXED
+        self.mixed = model.precision != snk.SNK_FP32
         self.params_lp = low_precision_copy(self.params, self.lay, model) if self.mixed else None
         self.grads = torch.zeros(n, dtype=torch.float32, device=device)
         self.m = torch.zeros(n, dtype=torch.float32, device=device)

@@ -100,6 +100,47 @@ def heightfield(seed, lo, hi, n_sin=8, amplitude=20.0, min_wavelength=24.0):
     return Heightfield(z_base, amp, k, phase, albedo, lo, hi, sun)
 
 
+@dataclass
+class Blocks:
+    """Urban-like scene: z(x, y) = H[i, j], the height of the raster cell
+    (i = row along y, j = column along x) of an n x n grid over the scene's xy
+    box that holds (x, y).  H is a ground level plus seeded axis-aligned
+    blocks (walls are vertical, roofs flat)."""
+    H: np.ndarray       # (n, n) cell heights, metres
+    albedo: np.ndarray  # (32, 32, 3) colour noise over the scene's xy box
+    lo: np.ndarray
+    hi: np.ndarray
+    sun: np.ndarray
+
+
+def blocks(seed, lo, hi, n=512, coverage=0.45, height=(5.0, 60.0), side=(0.01, 0.08)):
+    """Seeded blocks on an n x n raster: block heights U(height) above a ground
+    level at 10 % of the box height (scaled to the box when it is lower than
+    96 m), footprints U(side) x the box side per axis, drawn until about
+    `coverage` of the cells are covered (overlaps take the taller block)."""
+    rng = np.random.default_rng(seed)
+    lo = np.asarray(lo, float)
+    hi = np.asarray(hi, float)
+    zlen = hi[2] - lo[2]
+    s = min(1.0, zlen / 96.0)
+    ground = lo[2] + 0.1 * zlen
+    H = np.full((n, n), ground)
+    covered = np.zeros((n, n), bool)
+    while covered.mean() < coverage:
+        wx = max(1, int(rng.uniform(*side) * n))
+        wy = max(1, int(rng.uniform(*side) * n))
+        j0 = int(rng.integers(0, n - wx + 1))
+        i0 = int(rng.integers(0, n - wy + 1))
+        top = ground + s * rng.uniform(*height)
+        H[i0:i0 + wy, j0:j0 + wx] = np.maximum(H[i0:i0 + wy, j0:j0 + wx], top)
+        covered[i0:i0 + wy, j0:j0 + wx] = True
+    albedo = rng.uniform(0.15, 0.9, (32, 32, 3))
+    sun_az = rng.uniform(0, 2 * np.pi)
+    sun_el = np.deg2rad(rng.uniform(40, 70))
+    sun = np.array([np.cos(sun_el) * np.cos(sun_az), np.cos(sun_el) * np.sin(sun_az), np.sin(sun_el)])
+    return Blocks(H, albedo, lo, hi, sun)
+
+
 def pushbroom_cameras(seed, n_views, width, height, lo, hi, off_nadir=(5.0, 30.0),
                       kind=CAM_AFFINE, rpc_perturb=1e-3, footprint=1.0):
     """Seeded satellite-like views of the scene box [lo, hi].

@@ -8,7 +8,7 @@ draws; no step of the method is computed.
 from dataclasses import dataclass, field
 import numpy as np
 
-from . import (CAM_AFFINE, CAM_RPC3, Window, heightfield, pushbroom_cameras, random_pixels,
+from . import (CAM_AFFINE, CAM_RPC3, Window, blocks, heightfield, pushbroom_cameras, random_pixels,
                dirichlet_mix, pack_pixel, glorot_bound)
 
 
@@ -40,6 +40,9 @@ class Workload:
     seed: int = 0
     hidden: int = 64
     notes: str = ""
+    scene_kind: str = "sines"    # "blocks": raster blocks (synth.blocks) on a raster x raster grid
+    raster: int = 512
+    first_layer: str = "f16"     # "e4m3": 8-bit first-layer input, per-tensor scale from the batch
 
     @property
     def n_slots(self):
@@ -67,11 +70,19 @@ WORKLOADS = {
     "window2x2_full": Workload("window2x2_full", (512.0, 512.0, 96.0), 2, 2, 16, 2048, CAM_RPC3, (5.0, 30.0),
                                16, 2, 19, 16, 2048, 16, True, True, 524288, 128, 64, 128, mixed=True,
                                crop_margin=64, dirichlet=True),
+    # Mixed-precision stress: the 2x2 window over raster blocks 5-60 m tall on a 512 x 512 grid,
+    # off-nadir up to 40 degrees, 256 samples per ray, E4M3 first-layer input.
+    "window2x2_fp8": Workload("window2x2_fp8", (512.0, 512.0, 96.0), 2, 2, 16, 2048, CAM_RPC3, (5.0, 40.0),
+                              16, 2, 19, 16, 2048, 16, True, True, 524288, 256, 32, 256, mixed=True,
+                              crop_margin=64, dirichlet=True, scene_kind="blocks", first_layer="e4m3"),
     # Small cases for the oracle (seconds on a CPU).
     "tiny_tile": Workload("tiny_tile", (64.0, 64.0, 32.0), 1, 1, 4, 48, CAM_AFFINE, (5.0, 30.0),
                           4, 2, 10, 4, 32, 4, False, True, 96, 24, 24, 24),
     "tiny_window": Workload("tiny_window", (48.0, 48.0, 32.0), 2, 2, 6, 64, CAM_RPC3, (10.0, 35.0),
                             4, 2, 11, 4, 48, 16, True, True, 160, 32, 12, 32, crop_margin=4, dirichlet=True),
+    "tiny_window_fp8": Workload("tiny_window_fp8", (48.0, 48.0, 32.0), 2, 2, 6, 64, CAM_RPC3, (10.0, 40.0),
+                                4, 2, 11, 4, 48, 16, True, True, 160, 48, 8, 48, mixed=True, crop_margin=4,
+                                dirichlet=True, scene_kind="blocks", raster=64, first_layer="e4m3"),
 }
 
 
@@ -83,6 +94,8 @@ def get(name, **overrides):
 
 def scene(w):
     lo, hi = w.scene_box()
+    if w.scene_kind == "blocks":
+        return blocks(w.seed, lo, hi, n=w.raster)
     amp = 20.0 * min(1.0, w.tile[2] / 64.0) if w.tile[2] >= 32 else 8.0
     return heightfield(w.seed, lo, hi, amplitude=amp, min_wavelength=max(8.0, w.tile[0] / 10.0))
 

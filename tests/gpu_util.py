@@ -51,7 +51,7 @@ def small_crops(cams, size, seed=0):
 def model_config(w, hidden=64):
     return OS.ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, hidden=hidden,
                           geo_out=w.geo_out, colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots,
-                          K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max)
+                          K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max, first_layer=w.first_layer)
 
 
 @dataclasses.dataclass
