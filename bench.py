@@ -108,7 +108,7 @@ def field_forward_work(w, precision):
 
 # DRAM bytes per sample of each kernel measured by ncu (--set full) on the 32768-ray case of the
 # 512 m tile (tile-local traffic grows with the samples processed); null once a kernel changes.
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward"): 174.3, ("mixed", "field_forward"): 149.0,
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward"): 174.2, ("mixed", "field_forward"): 149.2,
                             ("fp32", "field_backward"): 736.6, ("fp32", "field_forward"): 42.5}
 
 

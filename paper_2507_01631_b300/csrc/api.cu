@@ -15,8 +15,6 @@ std::atomic<int64_t> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace snk
 
-constexpr int kStages = 5;
-
 struct snk_ctx {
   int device = 0;
   int sm_count = 148;

@@ -123,6 +123,42 @@ __device__ __forceinline__ int slot_of(const snk_state *st, int64_t s) {
 
 __device__ __forceinline__ void set_status(snk_state *st, uint32_t bit) { atomicOr(&st->status, bit); }
 
+// ---- x-adjacent corner pairs -------------------------------------------------
+// Corners (x, y, z) and (x + 1, y, z) of a cell have entries e0, e1.  When they
+// form one aligned pair {2k, 2k + 1} -- the dense index with x + ... even, or the
+// hash (whose x factor is 1) with x even -- one 8-byte load (FP16 features) or
+// one 16-byte reduction (binary32 gradients) serves both; otherwise two accesses.
+// The table and gradient blocks start on 16-byte boundaries (level sizes are
+// multiples of 8 entries).
+
+// v0 = table[e0], v1 = table[e1] (FP16 feature pairs).
+__device__ __forceinline__ void load_pair(const __half2 *tab, uint32_t e0, uint32_t e1, __half2 &v0, __half2 &v1) {
+  if ((e0 ^ e1) == 1u) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(tab + (e0 & ~1u)));
+    const uint32_t a = (e0 & 1u) ? u.y : u.x, b = (e0 & 1u) ? u.x : u.y;
+    v0 = *reinterpret_cast<const __half2 *>(&a);
+    v1 = *reinterpret_cast<const __half2 *>(&b);
+  } else {
+    v0 = __ldg(tab + e0);
+    v1 = __ldg(tab + e1);
+  }
+}
+
+// grad[e0] += w0 * d, grad[e1] += w1 * d (fire-and-forget reductions).
+__device__ __forceinline__ void red_pair(float2 *grad, uint32_t e0, uint32_t e1, float w0, float w1, float2 d) {
+  if ((e0 ^ e1) == 1u) {
+    const bool odd = e0 & 1u;
+    const float a = odd ? w1 : w0, b = odd ? w0 : w1;
+    float *q = reinterpret_cast<float *>(grad + (e0 & ~1u));
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(q), "f"(a * d.x), "f"(a * d.y), "f"(b * d.x),
+                 "f"(b * d.y)
+                 : "memory");
+  } else {
+    atomicAdd(grad + e0, make_float2(w0 * d.x, w0 * d.y));
+    atomicAdd(grad + e1, make_float2(w1 * d.x, w1 * d.y));
+  }
+}
+
 // ---- E4M3 (OCP 8-bit float: sign, 4 exponent bits with bias 7, 3 mantissa bits,
 // largest finite 448, no infinities) -----------------------------------------
 // Two binary32 values to an E4M3 pair (lo in the low byte): round to nearest

@@ -1,7 +1,8 @@
 // S3 + S4 (+ S7b, S7c), mixed precision on the 5th-generation tensor cores.
 //
 // Forward (per 128-sample tile, 256 threads): gather the FP16 hash-table
-// features of every level (Sec. 4.1, NGP) and interpolate them in FP32, store
+// features of every level (Sec. 4.1, NGP; x-adjacent corners that share an
+// aligned pair of entries in one 8-byte load) and interpolate them in FP32, store
 // them as FP16 into shared memory, then run the density MLP and the shared
 // colour MLP (Sec. 4.1) as a chain of tcgen05 MMAs, M = 128 samples, FP16
 // operands in shared memory, FP32 accumulators in tensor memory.  Each
@@ -10,7 +11,7 @@
 // global memory (64 bytes per sample) so that the backward does not re-gather
 // 512 bytes per sample from the tables.
 //
-// Backward (per tile, 256 threads, one CTA per SM): reload the features,
+// Backward (per tile, one CTA per SM): warps 0-7 reload the features,
 // recompute the MLP activations, then per layer two MMAs: the input gradient
 // dX = delta * W (W read MN-major from the same shared buffer the forward
 // reads K-major) and the weight gradient dW += delta^T * X (both operands read
@@ -18,12 +19,18 @@
 // M = 128 and the padding rows are never read).  The weight gradients stay in
 // tensor memory for the whole persistent loop and are added to the FP32
 // gradient buffer when the CTA moves to another slot and at exit.  The
-// feature gradients are scatter-added into the FP32 table gradients with
-// fire-and-forget float2 atomics.
+// feature gradient of a tile goes through a two-buffer shared-memory ring to
+// warps 8-11, which scatter-add it into the FP32 table gradients with
+// fire-and-forget reductions (one thread per sample; x-adjacent corners that
+// share an aligned pair of entries in one 16-byte reduction) while warps 0-7
+// run the next tile's MMA chain: the L1 reduction traffic of one tile overlaps
+// the tensor-core latency chain of the next.
 //
 // All mbarrier waits are bounded in time; a wait that gives up sets the
 // timeout status bit, stops the tile loop of the CTA, waits (bounded) for the
-// tensor core and frees the tensor memory before returning.
+// tensor core and frees the tensor memory before returning.  Decisions that
+// end the MMA warps' loop are made uniform over those warps (bar.red.or) and
+// also release the scatter warps' waits through a shared abort flag.
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -31,7 +38,9 @@ namespace snk {
 namespace {
 
 constexpr int TM = 128;  // samples per tile = MMA M
-constexpr int TT = 256;  // threads per CTA
+constexpr int TT = 256;  // threads of the MMA / epilogue warps (warps 0-7)
+constexpr int TS = 128;  // backward: threads of the scatter warps (warps 8-11), one per sample of a tile
+constexpr uint32_t kChainBar = 1;  // named barrier of the 256 MMA / epilogue threads
 // Split FP16 operands (Markidis et al. 2018): every activation and delta x
 // that feeds an MMA is carried as hi = fp16(x) and lo = fp16((x - hi) * 2^11);
 // a layer runs two MMAs, hi * W and lo * W, into separate tensor-memory
@@ -74,7 +83,14 @@ struct L {
   static constexpr int V2 = V1 + 64 * 16 * 2;                  // [64 x 64]
   static constexpr int V3 = V2 + 64 * 64 * 2;                  // [16 x 64]
   static constexpr int END = V3 + 16 * 64 * 2;
-  static constexpr int SMEM = END + 64;                        // + mbarrier and TMEM address
+  // backward: two [128 x (IN + 4)] binary32 feature-gradient buffers handed to the scatter warps
+  // (rows padded by 16 B against bank conflicts)
+  static constexpr int DFS = IN + 4;
+  static constexpr int DF = END;
+  static constexpr int DF_BYTES = BWD ? 2 * TM * DFS * 4 : 0;
+  // mbarriers (MMA commit, ring full[2] / empty[2]), TMEM address, tile info[2], abort flag
+  static constexpr int MISC = DF + DF_BYTES;
+  static constexpr int SMEM = MISC + 128;
   static constexpr uint32_t TCOLS = BWD ? 512 : 128;
   // tensor-memory columns: 0..63 accumulator of the high parts; C_DL the low parts
   static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
@@ -115,9 +131,9 @@ __device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, i
 }
 
 // Copy a row-major [rows x cols] 16-bit matrix from global into the core layout (R = rpad rows,
-// C = cpad columns), zero-padding, all threads.
+// C = cpad columns), zero-padding, by the TT MMA / epilogue threads.
 __device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, int rows, int cols, int rpad, int cpad) {
-  for (int e = threadIdx.x; e < rpad * cpad; e += blockDim.x) {
+  for (int e = threadIdx.x; e < rpad * cpad; e += TT) {
     const int r = e / cpad, c = e % cpad;
     const uint16_t v = (r < rows && c < cols) ? src[r * cols + c] : (uint16_t)0;
     *reinterpret_cast<uint16_t *>(dst + tc::core_off(r, c, rpad)) = v;
@@ -205,13 +221,25 @@ __device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, co
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
+// A tile handed from the MMA warps to the scatter warps.
+struct TileInfo {
+  int64_t ts;       // first slot-major sample of the tile
+  int32_t slot;
+  int32_t n_valid;  // rows 0 .. n_valid-1 are samples of the slot
+};
+
 template <int IN, int G, bool COL, bool BWD, bool Q8>
-__global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
+__global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
   using Y = L<IN, BWD>;
   constexpr int INP = Y::INP;
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + Y::END);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Y::END + 16);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + Y::MISC);
+  uint64_t *full = mbar + 1;   // [2] the MMA warps filled DF[b] (TT arrivals)
+  uint64_t *empty = mbar + 3;  // [2] the scatter warps drained DF[b] (TS arrivals)
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Y::MISC + 40);
+  TileInfo *info = reinterpret_cast<TileInfo *>(sm + Y::MISC + 48);  // [2]
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Y::MISC + 80);
+  float *dfbuf = reinterpret_cast<float *>(sm + Y::DF);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int r = 32 * (warp & 3) + lane;  // TMEM lane = tile row of this thread
   const int ch = warp >> 2;             // column half
@@ -223,11 +251,18 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
 
   if (t == 0) {
     tc::mbar_init(mbar, 1);
+    if (BWD) {
+      for (int b = 0; b < 2; ++b) {
+        tc::mbar_init(full + b, TT);
+        tc::mbar_init(empty + b, TS);
+      }
+    }
+    *abort_flag = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, Y::TCOLS);
   // zero every operand buffer once (padding columns are never written again)
-  for (int i = t; i < Y::END / 16; i += TT) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = t; i < Y::END / 16; i += blockDim.x) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -246,18 +281,18 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
   int cur_slot = -1;
   bool fresh = true;  // next dW MMAs start the accumulators
 
-  // all threads: wait for the MMAs committed last; CTA-uniform result
+  // MMA / epilogue threads: wait for the MMAs committed last; uniform result over those threads
   auto sync_mma = [&]() -> bool {
     const bool ok = tc::mbar_wait(mbar, phase);
     if (ok) phase ^= 1u;
     tc::fence_after_sync();
-    return __syncthreads_or(!ok) == 0;
+    return !tc::bar_or(kChainBar, TT, !ok);
   };
   // after an epilogue: make smem writes visible to the tensor core and TMEM reads ordered
   auto handoff = [&]() {
     tc::fence_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    tc::bar_sync(kChainBar, TT);
     tc::fence_after_sync();
   };
 
@@ -295,13 +330,64 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     fresh = true;
   };
 
+  if (BWD && t >= TT) {
+    // ---- scatter warps: add each tile's feature gradient, weighted by the trilinear
+    // weights, into the FP32 table gradients (float2 reductions, one thread per sample);
+    // they run while the MMA warps work on the next tile ----
+    const int s = t - TT;
+    int j = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      if (slot_of(st, r0 + tile * TM) < 0) continue;  // the MMA warps skip the same tiles
+      const int b = j & 1;
+      const int w = tc::mbar_wait_or_abort(full + b, (j >> 1) & 1, abort_flag);
+      if (w != 0) {
+        if (w == 2) {
+          atomicOr(&st_rw->status, kStatusTimeout);
+          *abort_flag = 1;
+        }
+        break;
+      }
+      const TileInfo ti = info[b];
+      if (s < ti.n_valid) {
+        const int64_t idx = ti.ts + s;
+        float xyz[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[idx * 3 + q];
+        const float *dfr = dfbuf + (b * TM + s) * Y::DFS;
+        float2 *gt0 = reinterpret_cast<float2 *>(a.grads + (int64_t)ti.slot * m.tile_params);
+        for (int l = 0; l < gp.L; ++l) {
+          const int N = gp.res[l];
+          const bool dense = gp.dense[l] != 0;
+          int ci[3];
+          float fr[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
+          const float2 d = *reinterpret_cast<const float2 *>(dfr + 2 * l);
+          float2 *gt = gt0 + gp.offset[l];
+          // corners c and c + 1 differ in x only; red_pair merges them when they share an aligned pair
+#pragma unroll
+          for (int c = 0; c < 8; c += 2) {
+            const uint32_t e0 = grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                           (uint32_t)gp.T - 1u);
+            const uint32_t e1 = grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                           (uint32_t)gp.T - 1u);
+            const float wyz = ((c & 2) ? fr[1] : 1.0f - fr[1]) * ((c & 4) ? fr[2] : 1.0f - fr[2]);
+            red_pair(gt, e0, e1, (1.0f - fr[0]) * wyz, fr[0] * wyz, d);
+          }
+        }
+      }
+      tc::mbar_arrive(empty + b);
+      ++j;
+    }
+  } else {
+  int jt = 0;  // tiles handed to the scatter warps
   for (int64_t tile = blockIdx.x; tile < n_tiles && !abort; tile += gridDim.x) {
     const int64_t ts = r0 + tile * TM;
     const int slot = slot_of(st, ts);
     if (slot < 0) continue;
     if (slot != cur_slot) {
       if (cur_slot >= 0) flush(cur_slot);
-      __syncthreads();
+      tc::bar_sync(kChainBar, TT);
       const uint16_t *P = a.params_lp + (int64_t)slot * m.tile_params;
       const uint16_t *C = a.params_lp + m.colour_base + (m.shared_colour ? 0 : (int64_t)slot * m.colour_params);
       load_weights(sm + Y::W1, P + m.w1, 64, IN, 64, INP);
@@ -391,9 +477,10 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
         if (sval) {
           __half2 hv[8];
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            hv[c] = __ldg(tab + grid_index(ci[0] + (c & 1), ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
-                                           (uint32_t)gp.T - 1u));
+          for (int c = 0; c < 8; c += 2)
+            load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
+                      grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
+                      hv[c], hv[c + 1]);
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
@@ -409,7 +496,7 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
         *reinterpret_cast<uint32_t *>(sm + Y::XL0 + tc::core_off(s, 2 * l, TM)) =
             pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
       }
-      __syncthreads();
+      tc::bar_sync(kChainBar, TT);
       // the tile's features (high and low parts), in the shared-memory layout, for the backward
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
         reinterpret_cast<uint4 *>(ftile)[i] = reinterpret_cast<const uint4 *>(sm + Y::X0)[i];
@@ -496,7 +583,7 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
         for (int k = 0; k < 3; ++k) rgb[k] = sigm(o[k]);
       }
       tc::fence_before_sync();
-      __syncthreads();
+      tc::bar_sync(kChainBar, TT);
       tc::fence_after_sync();
     }
 
@@ -607,52 +694,47 @@ __global__ void __launch_bounds__(TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a)
     abort = !sync_mma();
     if (abort) break;
     fresh = false;
-    // ---- scatter dfeat into the table gradients ----
+    // ---- hand dfeat (D_hi + 2^-11 D_lo, binary32) to the scatter warps through DF[b] ----
+    const int b = jt & 1;
+    int drained = 0;
+    if (t == 0 && jt >= 2) drained = tc::mbar_wait_or_abort(empty + b, ((jt >> 1) - 1) & 1, abort_flag);
+    if (t == 0 && drained == 2) atomicOr(&st_rw->status, kStatusTimeout);
+    abort = tc::bar_or(kChainBar, TT, drained != 0);
+    if (abort) break;
     const int c0 = ch * 16;
     if (c0 < IN) {
       float df[16], dfl[16];
       tc::ld16(trow + c0, df);
       tc::ld16(trow + Y::C_DL + c0, dfl);
       tc::wait_ld();
+      float *dst = dfbuf + (b * TM + r) * Y::DFS + c0;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) df[i] = fmaf(dfl[i], kLoInv, df[i]);
-      if (valid) {
-        float xyz[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[idx * 3 + q];
-        float2 *gt0 = reinterpret_cast<float2 *>(a.grads + (int64_t)slot * m.tile_params);
-        const int l0 = c0 / 2, l1 = min(gp.L, l0 + 8);
-        for (int l = l0; l < l1; ++l) {
-          const int N = gp.res[l];
-          const bool dense = gp.dense[l] != 0;
-          int ci[3];
-          float fr[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
-          const float d0 = df[2 * (l - l0)], d1 = df[2 * (l - l0) + 1];
-          float2 *gt = gt0 + gp.offset[l];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint32_t e = grid_index(ci[0] + (c & 1), ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
-                                          (uint32_t)gp.T - 1u);
-            const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
-                            ((c & 4) ? fr[2] : 1.0f - fr[2]);
-            atomicAdd(gt + e, make_float2(w * d0, w * d1));
-          }
-        }
-      }
+      for (int i = 0; i < 16; i += 4)
+        if (c0 + i < IN)
+          *reinterpret_cast<float4 *>(dst + i) =
+              make_float4(fmaf(dfl[i], kLoInv, df[i]), fmaf(dfl[i + 1], kLoInv, df[i + 1]),
+                          fmaf(dfl[i + 2], kLoInv, df[i + 2]), fmaf(dfl[i + 3], kLoInv, df[i + 3]));
     }
+    if (t == 0) {
+      int64_t nv = (slot_end < r1 ? slot_end : r1) - ts;
+      nv = nv < 0 ? 0 : (nv > TM ? TM : nv);
+      info[b] = TileInfo{ts, slot, (int32_t)nv};
+    }
+    tc::mbar_arrive(full + b);
+    ++jt;
     tc::fence_before_sync();
-    __syncthreads();
+    tc::bar_sync(kChainBar, TT);
     tc::fence_after_sync();
   }
 
   if (abort) {
     if (t == 0) atomicOr(&st_rw->status, kStatusTimeout);
+    *abort_flag = 1;             // releases scatter warps waiting for a tile
     tc::mbar_wait(mbar, phase);  // bounded: let any MMA still in flight finish before freeing TMEM
   } else if (BWD && cur_slot >= 0) {
     flush(cur_slot);
   }
+  }  // MMA / epilogue warps
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -674,7 +756,7 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
   int64_t grid = (int64_t)sm_count * per_sm;
   if (grid > max_tiles) grid = max_tiles;
   if (grid <= 0) return cudaSuccess;
-  k<<<(unsigned)grid, TT, Y::SMEM, st>>>(a);
+  k<<<(unsigned)grid, BWD ? TT + TS : TT, Y::SMEM, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -41,9 +41,10 @@ __global__ void k_gather_amax(const FieldArgs a) {
                              gp.offset[l];
         __half2 hv[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          hv[c] = __ldg(tab + grid_index(ci[0] + (c & 1), ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
-                                         (uint32_t)gp.T - 1u));
+        for (int c = 0; c < 8; c += 2)
+          load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
+                    grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
+                    hv[c], hv[c + 1]);
         float f0 = 0.f, f1 = 0.f;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {

@@ -88,6 +88,45 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
   }
 }
 
+// Arrive once on an mbarrier (release: this thread's earlier shared-memory writes are
+// visible to threads whose wait observes the phase completing).
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity that also gives up when *abort
+// becomes non-zero: 0 = completed, 1 = aborted, 2 = gave up after kWaitLimitNs.
+__device__ __forceinline__ int mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, const volatile int *abort) {
+  const uint32_t a = smem_u32(mbar);
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return 0;
+    if (*abort) return 1;
+    if (global_ns() - t0 > kWaitLimitNs) return 2;
+  }
+}
+
+// Named barrier `id` over the first n threads of the block (n a multiple of 32).
+__device__ __forceinline__ void bar_sync(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// Named barrier that also returns the OR of `pred` over the n participating threads.
+__device__ __forceinline__ bool bar_or(uint32_t id, uint32_t n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
 // Warp-wide: allocate ncols TMEM columns (power of two >= 32); the address is written to *dst (shared).
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
