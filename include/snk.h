@@ -192,8 +192,8 @@ const char *snk_last_error(const snk_ctx *ctx);
 /* Library version string (host, static). */
 const char *snk_version(void);
 /* Host only: sizeof of the ABI structs, in the order snk_camera, snk_window,
- * snk_model, snk_layout, snk_sampler, snk_adam, snk_params, snk_state, written
- * to sizes[0..n-1] (n <= 8).  Lets a binding check its struct mirrors.  Returns
+ * snk_model, snk_layout, snk_sampler, snk_adam, snk_params, snk_state,
+ * snk_tuning, written to sizes[0..n-1] (n <= 9).  Lets a binding check its struct mirrors.  Returns
  * the number written. */
 int snk_abi_sizes(int64_t *sizes, int n);
 
@@ -316,6 +316,35 @@ int snk_sample_segments_static(const snk_window *win, const snk_camera *cams, in
                                float *seg_t, uint32_t *seg_n, uint32_t *seg_off, float *smp_t, float *smp_dt,
                                float *smp_xyz, int64_t cap, snk_state *state, snk_stream_t stream, char *err,
                                int err_len);
+
+/* ---- launch shapes ------------------------------------------------------ */
+
+/* Launch shapes of the context's kernels (the paper has no counterpart: they
+ * change speed, never results beyond the order of float atomics). */
+typedef struct {
+    int32_t tc_fwd_ctas;       /* tensor-core forward: persistent CTAs per SM, 1 or 2 */
+    int32_t tc_fwd_levels;     /* tensor-core forward: levels whose corner loads are issued together, 1 or 2 */
+    int32_t fp32_ctas;         /* binary32 field kernels: persistent CTAs per SM, 1 or 2 */
+    int32_t composite_threads; /* compositing kernel: threads per block, 64..512, multiple of 32 */
+    int32_t sampler_threads;   /* ray and sample kernels: threads per block, 128..512, multiple of 32 */
+    int32_t tuned;             /* out: 1 if the values came from snk_autotune */
+    int32_t reserved[2];
+} snk_tuning;
+
+/* Current launch shapes of ctx (defaults until tuned or set). */
+int snk_get_tuning(snk_ctx *ctx, snk_tuning *out);
+/* Set the launch shapes of ctx (tuned is ignored); SNK_ERR_INVALID_ARG for a value out of range. */
+int snk_set_tuning(snk_ctx *ctx, const snk_tuning *in);
+/* Autotuner: time every candidate launch shape of the sampler, field-forward,
+ * field-backward (binary32 path) and compositing kernels on this batch (CUDA
+ * events on `stream`, one warm-up run and one or two timed runs each, one
+ * stage at a time) and keep the fastest for every later call on ctx.  Reads
+ * p->params / p->params_lp only: the caller's gradients, Adam state and step
+ * state are untouched (the tuner allocates its own scratch gradient buffer and
+ * state, and frees them).  Synchronises the stream; not graph-capturable.
+ * out (nullable) receives the chosen shapes. */
+int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
+                 const snk_sampler *sampler, const snk_params *p, snk_stream_t stream, snk_tuning *out);
 
 /* ---- diagnostics -------------------------------------------------------- */
 

@@ -29,6 +29,8 @@ struct snk_ctx {
                                // the E4M3 path uses the same bytes as [cap_samples + 128][32] binary32 features
   uint8_t *codes = nullptr;    // [cap_samples + 128][32] E4M3 first-layer codes
   uint32_t *amax = nullptr;    // [4] per-slot max |feature| (binary32 bits), E4M3 path
+  snk::Tuning tune;            // launch shapes (snk_autotune / snk_set_tuning)
+  bool tuned = false;
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -308,11 +310,11 @@ extern "C" {
 const char *snk_version(void) { return "libsnk 0.1 (sm_103a)"; }
 
 int snk_abi_sizes(int64_t *sizes, int n) {
-  const int64_t all[8] = {(int64_t)sizeof(snk_camera), (int64_t)sizeof(snk_window), (int64_t)sizeof(snk_model),
+  const int64_t all[9] = {(int64_t)sizeof(snk_camera), (int64_t)sizeof(snk_window), (int64_t)sizeof(snk_model),
                           (int64_t)sizeof(snk_layout), (int64_t)sizeof(snk_sampler), (int64_t)sizeof(snk_adam),
-                          (int64_t)sizeof(snk_params), (int64_t)sizeof(snk_state)};
+                          (int64_t)sizeof(snk_params), (int64_t)sizeof(snk_state), (int64_t)sizeof(snk_tuning)};
   if (!sizes || n < 0) return 0;
-  const int k = n < 8 ? n : 8;
+  const int k = n < 9 ? n : 9;
   for (int i = 0; i < k; ++i) sizes[i] = all[i];
   return k;
 }
@@ -432,7 +434,7 @@ int snk_sample_segments(snk_ctx *ctx, const snk_window *win, const uint32_t *pix
   rb.smp_dt = smp_dt;
   rb.smp_xyz = smp_xyz;
   SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, rb, cap, state,
-                                     (cudaStream_t)stream));
+                                     (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
 }
 
@@ -454,7 +456,7 @@ int snk_encode(snk_ctx *ctx, const snk_model *model, const snk_params *p, const 
   fa.S = S;
   fa.slot_only = -1;
   fa.mode = kEncodeOnly;
-  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream));
+  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
 }
 
@@ -495,7 +497,7 @@ int snk_mlp(snk_ctx *ctx, const snk_model *model, const snk_params *p, const flo
   fa.S = S;
   fa.slot_only = -1;
   fa.mode = kForward;
-  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream));
+  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
 }
 
@@ -518,7 +520,7 @@ int snk_mlp_backward(snk_ctx *ctx, const snk_model *model, const snk_params *p, 
   fa.S = S;
   fa.slot_only = -1;
   fa.mode = kBackward;
-  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream));
+  SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
 }
 
@@ -537,7 +539,7 @@ int snk_composite(snk_ctx *ctx, const float *sigma_rgb, const float *smp_t, cons
   ca.B = B;
   ca.out = out;
   ca.t_final = t_final;
-  SNK_CK(ctx, launch_composite(ca, (cudaStream_t)stream));
+  SNK_CK(ctx, launch_composite(ca, (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
 }
 
@@ -556,7 +558,7 @@ int snk_composite_backward(snk_ctx *ctx, const float *sigma_rgb, const float *sm
   ca.B = B;
   ca.g_rgb = g_rgb;
   ca.dsr = d_sigma_rgb;
-  SNK_CK(ctx, launch_composite(ca, (cudaStream_t)stream));
+  SNK_CK(ctx, launch_composite(ca, (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
 }
 
@@ -584,13 +586,13 @@ static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, c
       SNK_CK(ctx, cudaMemsetAsync(ctx->amax, 0, sizeof(uint32_t) * kMaxSlots, st));
       SNK_CK(ctx, launch_gather_amax(fa, ctx->sm_count, st));
     }
-    SNK_CK(ctx, launch_field_tc(fa, ctx->sm_count, st));
+    SNK_CK(ctx, launch_field_tc(fa, ctx->sm_count, st, ctx->tune));
     return SNK_OK;
   }
   // binary32 path: one launch chain per tile (slot), as a per-tile trainer issues them
   for (int k = 0; k < model->n_slots; ++k) {
     fa.slot_only = k;
-    SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, st));
+    SNK_CK(ctx, launch_field_fp32(fa, ctx->sm_count, st, ctx->tune));
   }
   return SNK_OK;
 }
@@ -617,7 +619,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   {
     StageMark m(ctx, 0, st);
     SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, ctx->rb, ctx->cap_samples, state,
-                                       st));
+                                       st, ctx->tune));
   }
   {
     StageMark m(ctx, 1, st);
@@ -638,7 +640,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   ca.train = 1;
   {
     StageMark m(ctx, 2, st);
-    SNK_CK(ctx, launch_composite(ca, st));
+    SNK_CK(ctx, launch_composite(ca, st, ctx->tune));
   }
   {
     StageMark m(ctx, 3, st);
@@ -698,7 +700,7 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   {
     StageMark m(ctx, 0, st);
     SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state,
-                                       st));
+                                       st, ctx->tune));
   }
   {
     StageMark m(ctx, 1, st);
@@ -715,8 +717,180 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   ca.state = state;
   {
     StageMark m(ctx, 2, st);
-    SNK_CK(ctx, launch_composite(ca, st));
+    SNK_CK(ctx, launch_composite(ca, st, ctx->tune));
   }
+  return SNK_OK;
+}
+
+static bool tuning_ok(const snk_tuning &t) {
+  auto mult32 = [](int v, int lo, int hi) { return v >= lo && v <= hi && v % 32 == 0; };
+  return (t.tc_fwd_ctas == 1 || t.tc_fwd_ctas == 2) && (t.tc_fwd_levels == 1 || t.tc_fwd_levels == 2) &&
+         (t.fp32_ctas == 1 || t.fp32_ctas == 2) && mult32(t.composite_threads, 64, 512) &&
+         mult32(t.sampler_threads, 128, 512);
+}
+static void to_abi(const snk::Tuning &u, bool tuned, snk_tuning *t) {
+  memset(t, 0, sizeof(*t));
+  t->tc_fwd_ctas = u.tc_fwd_ctas;
+  t->tc_fwd_levels = u.tc_fwd_levels;
+  t->fp32_ctas = u.fp32_ctas;
+  t->composite_threads = u.composite_threads;
+  t->sampler_threads = u.sampler_threads;
+  t->tuned = tuned ? 1 : 0;
+}
+
+int snk_get_tuning(snk_ctx *ctx, snk_tuning *out) {
+  if (!ctx || !out) return SNK_ERR_INVALID_ARG;
+  to_abi(ctx->tune, ctx->tuned, out);
+  return SNK_OK;
+}
+
+int snk_set_tuning(snk_ctx *ctx, const snk_tuning *in) {
+  if (!ctx || !in) return SNK_ERR_INVALID_ARG;
+  if (!tuning_ok(*in)) return fail(ctx, SNK_ERR_INVALID_ARG, "snk_set_tuning: value out of range");
+  ctx->tune.tc_fwd_ctas = in->tc_fwd_ctas;
+  ctx->tune.tc_fwd_levels = in->tc_fwd_levels;
+  ctx->tune.fp32_ctas = in->fp32_ctas;
+  ctx->tune.composite_threads = in->composite_threads;
+  ctx->tune.sampler_threads = in->sampler_threads;
+  ctx->tuned = false;
+  return SNK_OK;
+}
+
+int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
+                 const snk_sampler *sampler, const snk_params *p, snk_stream_t stream, snk_tuning *out) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  WinParams wp;
+  if ((rc = check_window(ctx, win, model->n_slots, &wp))) return rc;
+  SamplerParams sp;
+  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  sp.render = 0;
+  if ((rc = check_params(ctx, model, p, false))) return rc;
+  if (!pix || B < 1 || B > (1 << 22)) return fail(ctx, SNK_ERR_INVALID_ARG, "need pix and 1 <= B <= 2^22");
+  if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
+  if ((rc = ensure_ws(ctx, B, max_samples_for(win, sampler, B)))) return rc;
+  const cudaStream_t st = (cudaStream_t)stream;
+  // scratch: a per-step state, a gradient accumulator and a render output (the caller's are untouched)
+  void *scratch = nullptr;
+  const size_t grad_bytes = sizeof(float) * (size_t)lay.n_params;
+  const size_t bytes = sizeof(snk_state) + 256 + grad_bytes + 256 + sizeof(float) * 5 * (size_t)B;
+  if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SNK_ERR_OOM, "snk_autotune: scratch of %zu bytes could not be allocated", bytes);
+  }
+  snk_state *state = reinterpret_cast<snk_state *>(scratch);
+  float *grads = reinterpret_cast<float *>(static_cast<char *>(scratch) + (sizeof(snk_state) + 255) / 256 * 256);
+  float *rout = grads + (grad_bytes + 255) / 256 * 64;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const snk::Tuning saved = ctx->tune;
+  snk_params ps = *p;
+  ps.grads = grads;
+  rc = SNK_OK;
+  auto cuda_ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == SNK_OK) rc = fail(ctx, SNK_ERR_CUDA, "snk_autotune: %s", cudaGetErrorString(e));
+    return rc == SNK_OK;
+  };
+  // mean time of reps runs after one warm-up run; <0 on failure
+  auto time = [&](auto &&run, int reps) -> double {
+    if (run() != SNK_OK) return -1.0;
+    if (!cuda_ok(cudaEventRecord(e0, st))) return -1.0;
+    for (int i = 0; i < reps; ++i)
+      if (run() != SNK_OK) return -1.0;
+    if (!cuda_ok(cudaEventRecord(e1, st)) || !cuda_ok(cudaEventSynchronize(e1))) return -1.0;
+    float ms = 0.f;
+    if (!cuda_ok(cudaEventElapsedTime(&ms, e0, e1))) return -1.0;
+    return ms / reps;
+  };
+  auto sample = [&]() -> int {
+    if (launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state, st,
+                               ctx->tune) != cudaSuccess)
+      return fail(ctx, SNK_ERR_CUDA, "snk_autotune: sampling failed");
+    return SNK_OK;
+  };
+  auto field = [&](int mode) { return run_field(ctx, model, md, &ps, state, mode, st); };
+  CompositeArgs ca{};
+  ca.sigma_rgb = ctx->sigma_rgb;
+  ca.smp_t = ctx->rb.smp_t;
+  ca.smp_dt = ctx->rb.smp_dt;
+  ca.seg_n = ctx->rb.seg_n;
+  ca.seg_off = ctx->rb.seg_off;
+  ca.B = B;
+  ca.out = rout;
+  ca.state = state;
+  auto composite = [&]() -> int {
+    if (launch_composite(ca, st, ctx->tune) != cudaSuccess) return fail(ctx, SNK_ERR_CUDA, "snk_autotune: composite failed");
+    return SNK_OK;
+  };
+  do {
+    if (!cuda_ok(cudaEventCreate(&e0)) || !cuda_ok(cudaEventCreate(&e1))) break;
+    if (!cuda_ok(cudaMemsetAsync(state, 0, sizeof(snk_state), st))) break;
+    if (!cuda_ok(cudaMemsetAsync(ctx->dsr, 0, sizeof(float) * 4 * (size_t)ctx->cap_samples, st))) break;
+    // rays, segments and samples: threads per block
+    double best = -1.0;
+    int pick = saved.sampler_threads;
+    for (int nt : {128, 256, 512}) {
+      ctx->tune.sampler_threads = nt;
+      const double ms = time(sample, 2);
+      if (ms < 0) break;
+      if (best < 0 || ms < best) best = ms, pick = nt;
+    }
+    if (rc) break;
+    ctx->tune.sampler_threads = pick;
+    if (sample() != SNK_OK) break;  // leave this batch's samples in the workspace
+    // field kernels
+    if (model->precision != SNK_FP32) {
+      best = -1.0;
+      int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels;
+      for (int c : {1, 2})
+        for (int l : {1, 2}) {
+          if (l == 2 && model->precision == SNK_MIXED_E4M3) continue;  // no gather in that forward
+          ctx->tune.tc_fwd_ctas = c;
+          ctx->tune.tc_fwd_levels = l;
+          const double ms = time([&] { return field(kForward); }, 2);
+          if (ms < 0) break;
+          if (best < 0 || ms < best) best = ms, pc = c, pl = l;
+        }
+      if (rc) break;
+      ctx->tune.tc_fwd_ctas = pc;
+      ctx->tune.tc_fwd_levels = pl;
+    } else {
+      best = -1.0;
+      int pc = saved.fp32_ctas;
+      for (int c : {1, 2}) {
+        ctx->tune.fp32_ctas = c;
+        const double f = time([&] { return field(kForward); }, 1);
+        const double b = f < 0 ? -1.0 : time([&] { return field(kBackward); }, 1);
+        if (b < 0) break;
+        if (best < 0 || f + b < best) best = f + b, pc = c;
+      }
+      if (rc) break;
+      ctx->tune.fp32_ctas = pc;
+    }
+    if (field(kForward) != SNK_OK) break;
+    // compositing: threads per block
+    best = -1.0;
+    int pt = saved.composite_threads;
+    for (int nt : {64, 128, 256, 512}) {
+      ctx->tune.composite_threads = nt;
+      const double ms = time(composite, 2);
+      if (ms < 0) break;
+      if (best < 0 || ms < best) best = ms, pt = nt;
+    }
+    if (rc) break;
+    ctx->tune.composite_threads = pt;
+  } while (false);
+  if (rc == SNK_OK) cuda_ok(cudaStreamSynchronize(st));
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(scratch);
+  if (rc != SNK_OK) {
+    ctx->tune = saved;
+    return rc;
+  }
+  ctx->tuned = true;
+  if (out) to_abi(ctx->tune, true, out);
   return SNK_OK;
 }
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ float warp_rev_scan(float v, int lane) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_composite(const CompositeArgs a) {
+__global__ void __launch_bounds__(512) k_composite(const CompositeArgs a) {
   const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= a.B) return;
@@ -149,10 +149,11 @@ __global__ void __launch_bounds__(256) k_composite(const CompositeArgs a) {
 
 }  // namespace
 
-cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st) {
+cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st, const Tuning &tu) {
   if (a.B <= 0) return cudaSuccess;
   const int64_t threads = (int64_t)a.B * 32;
-  k_composite<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
+  const int nt = tu.composite_threads;
+  k_composite<<<(unsigned)((threads + nt - 1) / nt), nt, 0, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
 }
 
 template <int IN, int G, bool COL, int MODE>
-cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
+cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int ctas_per_sm) {
   using D = Dims<IN, G, COL>;
   const size_t smem = sizeof(float) * D::TOTAL;
   auto k = k_field_fp32<IN, G, COL, MODE>;
@@ -338,7 +338,7 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
     attr_done = true;
   }
   const int64_t max_tiles = (a.S + NS - 1) / NS;
-  int64_t grid = (int64_t)sm_count * 2;
+  int64_t grid = (int64_t)sm_count * ctas_per_sm;
   if (grid > max_tiles) grid = max_tiles;
   if (grid <= 0) return cudaSuccess;
   k<<<(unsigned)grid, NT, smem, st>>>(a);
@@ -347,18 +347,18 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
 }
 
 template <int IN, int G, bool COL>
-cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st) {
+cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, int c) {
   switch (a.mode) {
-    case kEncodeOnly: return launch_t<IN, G, COL, kEncodeOnly>(a, sm_count, st);
-    case kForward: return launch_t<IN, G, COL, kForward>(a, sm_count, st);
-    default: return launch_t<IN, G, COL, kBackward>(a, sm_count, st);
+    case kEncodeOnly: return launch_t<IN, G, COL, kEncodeOnly>(a, sm_count, st, c);
+    case kForward: return launch_t<IN, G, COL, kForward>(a, sm_count, st, c);
+    default: return launch_t<IN, G, COL, kBackward>(a, sm_count, st, c);
   }
 }
 
 template <int IN>
-cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st) {
-  if (a.m.colour) return launch_mode<IN, 16, true>(a, sm_count, st);
-  return launch_mode<IN, 4, false>(a, sm_count, st);
+cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st, int c) {
+  if (a.m.colour) return launch_mode<IN, 16, true>(a, sm_count, st, c);
+  return launch_mode<IN, 4, false>(a, sm_count, st, c);
 }
 
 // Thread per (sample, level): trilinear scatter-add of a feature gradient.
@@ -401,11 +401,12 @@ cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st) {
+cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
+  const int c = tu.fp32_ctas;
   switch (a.m.in_dim) {
-    case 8: return launch_in<8>(a, sm_count, st);
-    case 16: return launch_in<16>(a, sm_count, st);
-    case 32: return launch_in<32>(a, sm_count, st);
+    case 8: return launch_in<8>(a, sm_count, st, c);
+    case 16: return launch_in<16>(a, sm_count, st, c);
+    case 32: return launch_in<32>(a, sm_count, st, c);
     default: return cudaErrorInvalidValue;
   }
 }

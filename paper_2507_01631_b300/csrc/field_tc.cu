@@ -228,7 +228,7 @@ struct TileInfo {
   int32_t n_valid;  // rows 0 .. n_valid-1 are samples of the slot
 };
 
-template <int IN, int G, bool COL, bool BWD, bool Q8>
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL>
 __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
   using Y = L<IN, BWD>;
   constexpr int INP = Y::INP;
@@ -465,36 +465,51 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
         for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[sidx * 3 + q];
       }
       const __half2 *tab0 = reinterpret_cast<const __half2 *>(a.params_lp + (int64_t)slot * m.tile_params);
-      for (int l = half; l < gp.L; l += 2) {
-        const int N = gp.res[l];
-        const bool dense = gp.dense[l] != 0;
-        int ci[3];
-        float fr[3];
+      // KL levels per round: their corner loads are all issued before any is used
+      for (int l0 = half; l0 < gp.L; l0 += 2 * KL) {
+        __half2 hv[KL][8];
+        float fr[KL][3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
-        const __half2 *tab = tab0 + gp.offset[l];
-        float f0 = 0.f, f1 = 0.f;
-        if (sval) {
-          __half2 hv[8];
+        for (int k = 0; k < KL; ++k) {
+          const int l = l0 + 2 * k;
 #pragma unroll
-          for (int c = 0; c < 8; c += 2)
-            load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
-                      grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
-                      hv[c], hv[c + 1]);
+          for (int c = 0; c < 8; ++c) hv[k][c] = __float2half2_rn(0.f);
+          fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
+          if (l < gp.L && sval) {
+            const int N = gp.res[l];
+            const bool dense = gp.dense[l] != 0;
+            int ci[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[k][q]);
+            const __half2 *tab = tab0 + gp.offset[l];
+#pragma unroll
+            for (int c = 0; c < 8; c += 2)
+              load_pair(tab,
+                        grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
+                        grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                   (uint32_t)gp.T - 1u),
+                        hv[k][c], hv[k][c + 1]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+          const int l = l0 + 2 * k;
+          if (l >= gp.L) break;
+          float f0 = 0.f, f1 = 0.f;
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
-                            ((c & 4) ? fr[2] : 1.0f - fr[2]);
-            const float2 v = __half22float2(hv[c]);
+            const float w = ((c & 1) ? fr[k][0] : 1.0f - fr[k][0]) * ((c & 2) ? fr[k][1] : 1.0f - fr[k][1]) *
+                            ((c & 4) ? fr[k][2] : 1.0f - fr[k][2]);
+            const float2 v = __half22float2(hv[k][c]);
             f0 = fmaf(w, v.x, f0);
             f1 = fmaf(w, v.y, f1);
           }
+          const uint32_t hp = pack_h2(f0, f1);
+          const float2 hh = unpack_h2(hp);
+          *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = hp;
+          *reinterpret_cast<uint32_t *>(sm + Y::XL0 + tc::core_off(s, 2 * l, TM)) =
+              pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
         }
-        const uint32_t hp = pack_h2(f0, f1);
-        const float2 hh = unpack_h2(hp);
-        *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = hp;
-        *reinterpret_cast<uint32_t *>(sm + Y::XL0 + tc::core_off(s, 2 * l, TM)) =
-            pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
       }
       tc::bar_sync(kChainBar, TT);
       // the tile's features (high and low parts), in the shared-memory layout, for the backward
@@ -741,10 +756,10 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
   if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
 }
 
-template <int IN, int G, bool COL, bool BWD, bool Q8>
-cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL>
+cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_ctas) {
   using Y = L<IN, BWD>;
-  auto k = k_field_tc<IN, G, COL, BWD, Q8>;
+  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
@@ -752,7 +767,7 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
     attr_done = true;
   }
   const int64_t max_tiles = (a.S + TM - 1) / TM;
-  const int per_sm = BWD ? 1 : 2;
+  const int per_sm = BWD ? 1 : fwd_ctas;
   int64_t grid = (int64_t)sm_count * per_sm;
   if (grid > max_tiles) grid = max_tiles;
   if (grid <= 0) return cudaSuccess;
@@ -762,32 +777,34 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st) {
 }
 
 template <int IN, int G, bool COL, bool Q8>
-cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st) {
-  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8>(a, sm_count, st);
-  return launch_t<IN, G, COL, false, Q8>(a, sm_count, st);
+cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
+  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8, 1>(a, sm_count, st, 1);
+  // the E4M3 forward reads its features instead of gathering them: no gather shape to pick
+  if (!Q8 && tu.tc_fwd_levels == 2) return launch_t<IN, G, COL, false, Q8, 2>(a, sm_count, st, tu.tc_fwd_ctas);
+  return launch_t<IN, G, COL, false, Q8, 1>(a, sm_count, st, tu.tc_fwd_ctas);
 }
 
 template <int IN, int G, bool COL>
-cudaError_t launch_q(const FieldArgs &a, int sm_count, cudaStream_t st) {
-  if (a.m.e4m3) return launch_mode<IN, G, COL, true>(a, sm_count, st);
-  return launch_mode<IN, G, COL, false>(a, sm_count, st);
+cudaError_t launch_q(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
+  if (a.m.e4m3) return launch_mode<IN, G, COL, true>(a, sm_count, st, tu);
+  return launch_mode<IN, G, COL, false>(a, sm_count, st, tu);
 }
 
 template <int IN>
-cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st) {
-  if (a.m.colour) return launch_q<IN, 16, true>(a, sm_count, st);
-  return launch_q<IN, 4, false>(a, sm_count, st);
+cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
+  if (a.m.colour) return launch_q<IN, 16, true>(a, sm_count, st, tu);
+  return launch_q<IN, 4, false>(a, sm_count, st, tu);
 }
 
 }  // namespace
 
-cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st) {
+cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
   if (a.mode == kEncodeOnly || a.feat_lp == nullptr || a.params_lp == nullptr) return cudaErrorInvalidValue;
   if (a.m.e4m3 && (a.feat32 == nullptr || a.codes == nullptr || a.amax == nullptr)) return cudaErrorInvalidValue;
   switch (a.m.in_dim) {
-    case 8: return launch_in<8>(a, sm_count, st);
-    case 16: return launch_in<16>(a, sm_count, st);
-    case 32: return launch_in<32>(a, sm_count, st);
+    case 8: return launch_in<8>(a, sm_count, st, tu);
+    case 16: return launch_in<16>(a, sm_count, st, tu);
+    case 32: return launch_in<32>(a, sm_count, st, tu);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -4,6 +4,15 @@
 
 namespace snk {
 
+// Launch shapes picked by snk_autotune (defaults: the measured best on the 2x2 window).
+struct Tuning {
+  int tc_fwd_ctas = 2;          // tensor-core forward: persistent CTAs per SM (1, 2)
+  int tc_fwd_levels = 1;        // tensor-core forward: levels whose corner loads are issued together (1, 2)
+  int fp32_ctas = 2;            // binary32 field kernels: persistent CTAs per SM (1, 2)
+  int composite_threads = 256;  // compositing: threads per block (64 .. 512, multiple of 32)
+  int sampler_threads = 256;    // ray and sample kernels: threads per block (128 .. 512, multiple of 32)
+};
+
 // Adds n to the library-wide count of launched kernels (snk_launch_count).
 void count_launches(int n);
 
@@ -26,7 +35,7 @@ struct RayBuffers {
 int scan_blocks(int B);
 cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinParams &win, const SamplerParams &smp,
                                    const uint32_t *pix, int B, int need_targets, const RayBuffers &rb, int64_t cap,
-                                   snk_state *state, cudaStream_t st);
+                                   snk_state *state, cudaStream_t st, const Tuning &tu = Tuning());
 
 // Everything a field kernel needs to know about a model.
 struct ModelDev {
@@ -61,8 +70,8 @@ struct FieldArgs {
   int32_t slot_only;          // -1: every slot; k: only slot k (per-tile launches)
   int32_t mode;
 };
-cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st);
-cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st);
+cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu = Tuning());
+cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu = Tuning());
 // Scatter-add feat_in (read as dfeat [S][L*F]) into the table gradients.
 cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st);
 // E4M3 path, first pass: binary32 features from the FP16 tables into feat32 and
@@ -87,7 +96,7 @@ struct CompositeArgs {
   snk_state *state;
   int32_t train;          // 1: MSE loss against targets, gradient scaled by the loss scale
 };
-cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st);
+cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st, const Tuning &tu = Tuning());
 
 struct AdamArgs {
   float *params;

@@ -82,7 +82,7 @@ __device__ __forceinline__ Slab slab(const float o[3], const float d[3], const f
 }
 
 // One thread per ray: camera -> (o, d) -> acceptance -> <= 3 segments -> K per segment.
-__global__ void k_rays(const DevView *__restrict__ views, int n_views, WinParams win, SamplerParams smp,
+__global__ void __launch_bounds__(512) k_rays(const DevView *__restrict__ views, int n_views, WinParams win, SamplerParams smp,
                        const uint32_t *__restrict__ pix, int B, int need_targets, float *__restrict__ ray_od,
                        uint8_t *__restrict__ ray_ok, uint8_t *__restrict__ seg_slot, float *__restrict__ seg_t,
                        uint32_t *__restrict__ seg_n, uint32_t *__restrict__ cnt, snk_state *state) {
@@ -284,7 +284,7 @@ __global__ void k_scan_top(uint32_t *__restrict__ block_tot, int nb, int n_slots
 }
 
 // Warp per ray: segment offsets, then t, delta and tile-local xyz of every sample.
-__global__ void k_samples(const float *__restrict__ ray_od, const uint8_t *__restrict__ seg_slot,
+__global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_od, const uint8_t *__restrict__ seg_slot,
                           const float *__restrict__ seg_t, const uint32_t *__restrict__ seg_n,
                           const uint32_t *__restrict__ excl, const uint32_t *__restrict__ block_tot, int nb, int B,
                           WinParams win, SamplerParams smp, const snk_state *__restrict__ state,
@@ -340,16 +340,17 @@ int scan_blocks(int B) { return (B + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinParams &win, const SamplerParams &smp,
                                    const uint32_t *pix, int B, int need_targets, const RayBuffers &rb, int64_t cap,
-                                   snk_state *state, cudaStream_t st) {
+                                   snk_state *state, cudaStream_t st, const Tuning &tu) {
   if (B <= 0) return cudaSuccess;
-  k_rays<<<(B + 255) / 256, 256, 0, st>>>(views, n_views, win, smp, pix, B, need_targets, rb.ray_od, rb.ray_ok,
+  const int nt = tu.sampler_threads;
+  k_rays<<<(B + nt - 1) / nt, nt, 0, st>>>(views, n_views, win, smp, pix, B, need_targets, rb.ray_od, rb.ray_ok,
                                           rb.seg_slot, rb.seg_t, rb.seg_n, rb.cnt, state);
   const int nb = scan_blocks(B);
   const dim3 g(nb, win.n_slots + 1);
   k_scan_local<<<g, kScanThreads, 0, st>>>(rb.cnt, B, win.n_slots, rb.excl, rb.block_tot);
   k_scan_top<<<1, 32 * (kMaxSlots + 1), 0, st>>>(rb.block_tot, nb, win.n_slots, cap, state);
   const int64_t threads = (int64_t)B * 32;
-  k_samples<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n, rb.excl,
+  k_samples<<<(unsigned)((threads + nt - 1) / nt), nt, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n, rb.excl,
                                                                 rb.block_tot, nb, B, win, smp, state, rb.seg_off,
                                                                 rb.smp_t, rb.smp_dt, rb.smp_xyz);
   count_launches(4);

@@ -63,7 +63,13 @@ class SnkState(Structure):
                 ("slot_base", c_uint32 * 5), ("slot_count", c_uint32 * 4), ("reserved", c_uint32 * 3)]
 
 
-STRUCTS = [SnkCamera, SnkWindow, SnkModel, SnkLayout, SnkSampler, SnkAdam, SnkParams, SnkState]
+class SnkTuning(Structure):
+    _fields_ = [("tc_fwd_ctas", c_int32), ("tc_fwd_levels", c_int32), ("fp32_ctas", c_int32),
+                ("composite_threads", c_int32), ("sampler_threads", c_int32), ("tuned", c_int32),
+                ("reserved", c_int32 * 2)]
+
+
+STRUCTS = [SnkCamera, SnkWindow, SnkModel, SnkLayout, SnkSampler, SnkAdam, SnkParams, SnkState, SnkTuning]
 STATE_WORDS = ctypes.sizeof(SnkState) // 4
 
 _P = c_void_p
@@ -91,6 +97,10 @@ SIGNATURES = {
                            POINTER(SnkParams), _P, _P, _P]),
     "snk_sync_status": (c_int, [_P, _P, _P]),
     "snk_quantize_e4m3": (c_int, [_P, _P, c_int64, c_float, _P, _P]),
+    "snk_get_tuning": (c_int, [_P, POINTER(SnkTuning)]),
+    "snk_set_tuning": (c_int, [_P, POINTER(SnkTuning)]),
+    "snk_autotune": (c_int, [_P, POINTER(SnkModel), POINTER(SnkWindow), _P, c_int, POINTER(SnkSampler),
+                             POINTER(SnkParams), _P, POINTER(SnkTuning)]),
     "snk_sample_segments_static": (c_int, [POINTER(SnkWindow), POINTER(SnkCamera), c_int, _P, c_int,
                                            POINTER(SnkSampler), _P, _P, _P, _P, _P, _P, _P, _P, _P, c_int64, _P, _P,
                                            c_char_p, c_int]),
@@ -241,6 +251,25 @@ class Context:
         calls = (c_int64 * 5)()
         self.call("snk_stage_times", ms, calls, 5)
         return {n: (ms[i], calls[i]) for i, n in enumerate(STAGES)}
+
+    def tuning(self):
+        t = SnkTuning()
+        self.call("snk_get_tuning", ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in SnkTuning._fields_ if k != "reserved"}
+
+    def set_tuning(self, **values):
+        t = SnkTuning()
+        self.call("snk_get_tuning", ctypes.byref(t))
+        for k, v in values.items():
+            setattr(t, k, int(v))
+        self.call("snk_set_tuning", ctypes.byref(t))
+
+    def autotune(self, model, window, pix, sampler, params_struct, stream=None):
+        """Pick the context's launch shapes on this batch (snk_autotune); returns them."""
+        t = SnkTuning()
+        self.call("snk_autotune", ctypes.byref(model), ctypes.byref(window), ptr(pix), int(pix.numel()),
+                  ctypes.byref(sampler), ctypes.byref(params_struct), stream_handle(stream), ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in SnkTuning._fields_ if k != "reserved"}
 
     def sync_status(self, state, stream=None):
         return self.lib.snk_sync_status(self.h, ptr(state), stream_handle(stream))

@@ -64,6 +64,11 @@ class Trainer:
                       int(pix.numel()), ctypes.byref(self.sampler), ctypes.byref(self.p_struct),
                       snk.ptr(self.state), snk.ptr(out), snk.stream_handle(stream))
 
+    def autotune(self, pix, stream=None):
+        """Pick the context's launch shapes on this batch (snk_autotune); the
+        trainer's parameters, gradients and Adam state are not modified."""
+        return self.ctx.autotune(self.model, self.window, pix, self.sampler, self.p_struct, stream)
+
     def read_state(self):
         s = self.state.cpu().numpy()
         out = {}

@@ -1,0 +1,87 @@
+"""Launch shapes (snk_autotune / snk_set_tuning): every shape computes the same
+step -- rendered outputs bit-identical, gradients equal up to the order of
+float atomics -- and the autotuner leaves the caller's training state alone."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2507_01631_b300 import build, snk
+from paper_2507_01631_b300.trainer import Trainer, model_from_workload
+from gpu_util import make_case, normwise
+
+pytestmark = pytest.mark.gpu
+DEFAULT = dict(tc_fwd_ctas=2, tc_fwd_levels=1, fp32_ctas=2, composite_threads=256, sampler_threads=256)
+ALTERNATIVES = [("tc_fwd_ctas", 1), ("tc_fwd_levels", 2), ("fp32_ctas", 1), ("composite_threads", 64),
+                ("composite_threads", 512), ("sampler_threads", 128), ("sampler_threads", 512)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    c = snk.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _step(ctx, case, precision):
+    crops = [dev(t.astype(np.float32)) for t in case.targets]
+    ctx.set_views(case.cams, crops)
+    w = case.w
+    tr = Trainer(ctx, model_from_workload(w, precision), snk.window_struct(w.window()),
+                 snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, 5, 0), case.params)
+    out = torch.zeros(len(case.pix) * 5, dtype=torch.float32, device="cuda")
+    tr.train_step(dev(case.pix.view(np.int32)), out)
+    assert ctx.sync_status(tr.state) == snk.SNK_OK
+    return out.cpu().numpy(), tr.m.cpu().numpy().astype(np.float64), tr.read_state()["loss"]
+
+
+@pytest.mark.parametrize("precision", [snk.SNK_MIXED, snk.SNK_FP32])
+def test_every_launch_shape_computes_the_same_step(ctx, precision):
+    case = make_case("window2x2_full", n_rays=384, crop=48, table_scale=0.3)
+    ctx.set_tuning(**DEFAULT)
+    out0, m0, loss0 = _step(ctx, case, precision)
+    for key, val in ALTERNATIVES:
+        ctx.set_tuning(**dict(DEFAULT, **{key: val}))
+        out, m, loss = _step(ctx, case, precision)
+        assert np.array_equal(out, out0), (key, val)
+        assert abs(loss - loss0) <= 1e-6 * abs(loss0), (key, val)
+        assert normwise(m, m0) < 1e-5, (key, val)
+    ctx.set_tuning(**DEFAULT)
+
+
+@pytest.mark.parametrize("precision", [snk.SNK_MIXED, snk.SNK_FP32])
+def test_autotune_picks_valid_shapes_and_leaves_the_training_state(ctx, precision):
+    case = make_case("window2x2_full", n_rays=2048, crop=48, table_scale=0.3)
+    crops = [dev(t.astype(np.float32)) for t in case.targets]
+    ctx.set_views(case.cams, crops)
+    w = case.w
+    tr = Trainer(ctx, model_from_workload(w, precision), snk.window_struct(w.window()),
+                 snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, 5, 0), case.params)
+    before = [x.clone() for x in (tr.params, tr.grads, tr.m, tr.v, tr.steps, tr.state)]
+    t = tr.autotune(dev(case.pix.view(np.int32)))
+    torch.cuda.synchronize()
+    assert t["tuned"] == 1
+    assert t["tc_fwd_ctas"] in (1, 2) and t["tc_fwd_levels"] in (1, 2) and t["fp32_ctas"] in (1, 2)
+    assert t["composite_threads"] in (64, 128, 256, 512) and t["sampler_threads"] in (128, 256, 512)
+    assert ctx.tuning() == t
+    for a, b in zip(before, (tr.params, tr.grads, tr.m, tr.v, tr.steps, tr.state)):
+        assert torch.equal(a, b)
+    # a step with the tuned shapes still trains
+    tr.train_step(dev(case.pix.view(np.int32)))
+    assert ctx.sync_status(tr.state) == snk.SNK_OK
+    ctx.set_tuning(**DEFAULT)
+    assert ctx.tuning()["tuned"] == 0
+
+
+def test_out_of_range_tuning_is_rejected(ctx):
+    for key, val in [("tc_fwd_ctas", 3), ("tc_fwd_levels", 4), ("composite_threads", 96 + 1),
+                     ("sampler_threads", 1024), ("fp32_ctas", 0)]:
+        with pytest.raises(RuntimeError):
+            ctx.set_tuning(**dict(DEFAULT, **{key: val}))
+    assert ctx.tuning()["tc_fwd_ctas"] == DEFAULT["tc_fwd_ctas"]
