@@ -317,6 +317,26 @@ int snk_sample_segments_static(const snk_window *win, const snk_camera *cams, in
                                float *smp_xyz, int64_t cap, snk_state *state, snk_stream_t stream, char *err,
                                int err_len);
 
+/* ---- tile residency (snake sweep, Sec. 4.4) ------------------------------ */
+
+/* Host only: bytes of one parked tile of `model`, a contiguous block laid out
+ * (offsets rounded up to 256 bytes) as
+ *   params (tile_params x f32) | adam_m (f32) | adam_v (f32) |
+ *   params_lp (tile_params x u16; unused for SNK_FP32) | Adam step count (i32). */
+int snk_tile_bytes(const snk_model *model, int64_t *bytes);
+/* Copy the trainable state of parameter slot `slot` (its block of params,
+ * params_lp, adam_m, adam_v and its step count) into dst, a block of
+ * snk_tile_bytes bytes in pinned host memory or device memory (cudaMemcpyAsync
+ * on `stream`, cudaMemcpyDefault: asynchronous for pinned or device memory).
+ * The slot's gradients are not copied (they are zero between steps).  The slot
+ * keeps its contents; the caller may then unpark another tile into it.
+ * SNK_ERR_INVALID_ARG for a bad slot, model or NULL pointer. */
+int snk_tile_park(snk_ctx *ctx, const snk_model *model, const snk_params *p, int slot, void *dst,
+                  snk_stream_t stream);
+/* Reverse of snk_tile_park: load a parked block into slot `slot`. */
+int snk_tile_unpark(snk_ctx *ctx, const snk_model *model, const snk_params *p, int slot, const void *src,
+                    snk_stream_t stream);
+
 /* ---- launch shapes ------------------------------------------------------ */
 
 /* Launch shapes of the context's kernels (the paper has no counterpart: they

@@ -167,10 +167,10 @@ def field_forward(cfg, flat, smp):
     return sigma, rgb, saved
 
 
-def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, seed, iteration):
+def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, seed, iteration, lr=None):
     """One training step.  targets: list of per-view crop images (h, w, 3).
     steps: per-optimiser Adam step counts before this step (updated copy is
-    returned in extra["steps"])."""
+    returned in extra["steps"]).  lr: Adam learning rate (I-NGP's 1e-2 unless given)."""
     o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, False)
     sigma, rgb_s, saved = field_forward(cfg, flat, smp)
     rgb, depth, opac, tfin, _ = render.composite(sigma, rgb_s, smp.t.astype(np.float64),
@@ -200,7 +200,8 @@ def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, s
         steps[gi] += 1
         l2 = np.zeros(b - a)
         l2[mlp_a - a:] = adam.L2_MLP
-        w, mm, vv = adam.step(flat[a:b], grad[a:b], m_state[a:b], v_state[a:b], steps[gi], l2=l2)
+        w, mm, vv = adam.step(flat[a:b], grad[a:b], m_state[a:b], v_state[a:b], steps[gi],
+                              lr=adam.LR if lr is None else lr, l2=l2)
         new[a:b], m_new[a:b], v_new[a:b] = w, mm, vv
     res = StepResult(seg, smp, sigma, rgb_s, rgb, depth, opac, tfin, loss, grad, dsigma, drgb, new, m_new, v_new)
     res.extra["steps"] = steps

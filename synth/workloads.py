@@ -43,20 +43,28 @@ class Workload:
     scene_kind: str = "sines"    # "blocks": raster blocks (synth.blocks) on a raster x raster grid
     raster: int = 512
     first_layer: str = "f16"     # "e4m3": 8-bit first-layer input, per-tensor scale from the batch
+    grid: tuple = (0, 0)         # tiles of the whole scene for a snake sweep; (0, 0): the window is the scene
 
     @property
     def n_slots(self):
         return self.nx * self.ny
 
+    def grid_tiles(self):
+        return self.grid if self.grid[0] > 0 else (self.nx, self.ny)
+
     def scene_box(self):
+        gx, gy = self.grid_tiles()
         lo = np.array([0.0, 0.0, 0.0])
-        hi = np.array([self.nx * self.tile[0], self.ny * self.tile[1], self.tile[2]])
+        hi = np.array([gx * self.tile[0], gy * self.tile[1], self.tile[2]])
         return lo, hi
 
-    def window(self):
+    def window(self, pos=(0, 0), slot=(0, 1, 2, 3)):
+        """The window whose lower-left tile is tile `pos` of the grid; slot[iy * nx + ix]
+        is the parameter slot of the window's tile (ix, iy)."""
         lo, hi = self.scene_box()
-        return Window(origin=lo.copy(), tile_size=np.array(self.tile, float), nx=self.nx, ny=self.ny,
-                      scene_lo=lo, scene_hi=hi, slot=tuple(range(4)))
+        origin = np.array([pos[0] * self.tile[0], pos[1] * self.tile[1], 0.0])
+        return Window(origin=origin, tile_size=np.array(self.tile, float), nx=self.nx, ny=self.ny,
+                      scene_lo=lo, scene_hi=hi, slot=tuple(slot))
 
 
 WORKLOADS = {
@@ -75,11 +83,19 @@ WORKLOADS = {
     "window2x2_fp8": Workload("window2x2_fp8", (512.0, 512.0, 96.0), 2, 2, 16, 2048, CAM_RPC3, (5.0, 40.0),
                               16, 2, 19, 16, 2048, 16, True, True, 524288, 256, 32, 256, mixed=True,
                               crop_margin=64, dirichlet=True, scene_kind="blocks", first_layer="e4m3"),
+    # Snake sweep over an 8 x 8 grid of 512 x 512 x 128 m tiles (4096 x 4096 x 128 m scene), 32 RPC-like
+    # views at 4096 px, 262144 rays per iteration on the active 2 x 2 window.
+    "sweep_grid8": Workload("sweep_grid8", (512.0, 512.0, 128.0), 2, 2, 32, 4096, CAM_RPC3, (5.0, 30.0),
+                            16, 2, 19, 16, 2048, 16, True, True, 262144, 128, 64, 128, mixed=True,
+                            crop_margin=64, dirichlet=True, grid=(8, 8)),
     # Small cases for the oracle (seconds on a CPU).
     "tiny_tile": Workload("tiny_tile", (64.0, 64.0, 32.0), 1, 1, 4, 48, CAM_AFFINE, (5.0, 30.0),
                           4, 2, 10, 4, 32, 4, False, True, 96, 24, 24, 24),
     "tiny_window": Workload("tiny_window", (48.0, 48.0, 32.0), 2, 2, 6, 64, CAM_RPC3, (10.0, 35.0),
                             4, 2, 11, 4, 48, 16, True, True, 160, 32, 12, 32, crop_margin=4, dirichlet=True),
+    "tiny_sweep": Workload("tiny_sweep", (32.0, 32.0, 24.0), 2, 2, 6, 96, CAM_RPC3, (10.0, 30.0),
+                           4, 2, 10, 4, 32, 16, True, True, 96, 16, 4, 16, crop_margin=4, dirichlet=True,
+                           grid=(3, 3)),
     "tiny_window_fp8": Workload("tiny_window_fp8", (48.0, 48.0, 32.0), 2, 2, 6, 64, CAM_RPC3, (10.0, 40.0),
                                 4, 2, 11, 4, 48, 16, True, True, 160, 48, 8, 48, mixed=True, crop_margin=4,
                                 dirichlet=True, scene_kind="blocks", raster=64, first_layer="e4m3"),
@@ -106,11 +122,11 @@ def cameras(w):
                              kind=w.cam_kind)
 
 
-def tile_crops(w, cams):
-    """Per view and tile: pixel rectangle (r0, c0, h, w) that contains the
-    image of the tile's 8 corners, widened by the crop margin and clipped to
-    the image (the crops of Sec. 4.3, built from the affine part of each
-    synthetic camera as it was drawn)."""
+def tile_crops(w, cams, pos=(0, 0)):
+    """Per view and tile of the window at grid position `pos`: pixel rectangle
+    (r0, c0, h, w) that contains the image of the tile's 8 corners, widened by
+    the crop margin and clipped to the image (the crops of Sec. 4.3, built from
+    the affine part of each synthetic camera as it was drawn)."""
     out = []
     for cam in cams:
         A = np.array([[cam.a[1], cam.a[2]], [cam.b[1], cam.b[2]]])
@@ -118,8 +134,8 @@ def tile_crops(w, cams):
         rects = []
         for iy in range(w.ny):
             for ix in range(w.nx):
-                xs = [ix * w.tile[0], (ix + 1) * w.tile[0]]
-                ys = [iy * w.tile[1], (iy + 1) * w.tile[1]]
+                xs = [(pos[0] + ix) * w.tile[0], (pos[0] + ix + 1) * w.tile[0]]
+                ys = [(pos[1] + iy) * w.tile[1], (pos[1] + iy + 1) * w.tile[1]]
                 rc = []
                 for x in xs:
                     for y in ys:
@@ -136,15 +152,16 @@ def tile_crops(w, cams):
     return out
 
 
-def batch(w, cams, seed, n_rays=None):
-    """Packed pixel ids of one random ray batch.  Without a Dirichlet mix the
-    pixels are uniform over every view's crop; with it, n ~ Multinomial(n_rays,
-    p), p ~ Dirichlet(0.5) rays are drawn from the crops of each tile."""
+def batch(w, cams, seed, n_rays=None, pos=(0, 0)):
+    """Packed pixel ids of one random ray batch for the window at grid position
+    `pos`.  Without a Dirichlet mix the pixels are uniform over every view's
+    crop; with it, n ~ Multinomial(n_rays, p), p ~ Dirichlet(0.5) rays are drawn
+    from the crops of each tile of the window."""
     n_rays = w.n_rays if n_rays is None else n_rays
     if not w.dirichlet:
         return random_pixels(seed, n_rays, cams)
     counts, _ = dirichlet_mix(seed, n_rays, w.n_slots)
-    crops = tile_crops(w, cams)
+    crops = tile_crops(w, cams, pos)
     rng = np.random.default_rng(seed + 7919)
     parts = []
     for t, n in enumerate(counts):
