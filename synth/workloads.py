@@ -143,8 +143,9 @@ def tile_crops(w, cams, pos=(0, 0)):
                             cc, rr = Ainv @ np.array([x - cam.a[0] - cam.a[3] * h, y - cam.b[0] - cam.b[3] * h])
                             rc.append((rr, cc))
                 rc = np.array(rc)
-                r0 = int(max(0, np.floor(rc[:, 0].min()) - w.crop_margin))
-                c0 = int(max(0, np.floor(rc[:, 1].min()) - w.crop_margin))
+                # a window outside the image gets an empty rectangle at the image border
+                r0 = int(min(cam.height, max(0, np.floor(rc[:, 0].min()) - w.crop_margin)))
+                c0 = int(min(cam.width, max(0, np.floor(rc[:, 1].min()) - w.crop_margin)))
                 r1 = int(min(cam.height, np.ceil(rc[:, 0].max()) + w.crop_margin))
                 c1 = int(min(cam.width, np.ceil(rc[:, 1].max()) + w.crop_margin))
                 rects.append((r0, c0, max(0, r1 - r0), max(0, c1 - c0)))
