@@ -317,6 +317,37 @@ int snk_sample_segments_static(const snk_window *win, const snk_camera *cams, in
                                float *smp_xyz, int64_t cap, snk_state *state, snk_stream_t stream, char *err,
                                int err_len);
 
+/* ---- crops and ray pool of a window (Sec. 4.3, Sec. 4.4) ----------------- */
+
+/* Image crops from ground tiles (Sec. 4.3): every view of the context
+ * projects the 8 corners of each tile of the window (x, y of the tile's
+ * corners, h = z_min and z_max) to continuous pixel coordinates and takes
+ * rows [floor(min) - margin, ceil(max) + margin) and likewise columns,
+ * clipped to the image (an empty rectangle if the tile is outside it).  The
+ * projection solves localisation(row, col, h) = (x, y) by Newton's method in
+ * binary64 (forward-difference Jacobian with one-pixel steps, 16 iterations
+ * from the image centre).  Device outputs: tile_rects [n_views][4][4] =
+ * (r0, c0, h, w) of window tile k = iy * nx + ix (zeros for k >= nx * ny),
+ * view_rects [n_views][4] = the bounding rectangle of the view's non-empty
+ * tile rectangles ((0, 0, 0, 0) if none). */
+int snk_build_crops(snk_ctx *ctx, const snk_window *win, int margin, int32_t *tile_rects, int32_t *view_rects,
+                    snk_stream_t stream);
+/* Ray pool of the window: the packed pixels (view << 24 | row << 12 | col) of
+ * every view's rectangle in view_rects (device, as written by
+ * snk_build_crops) whose rays the window accepts (the acceptance of the
+ * training step, Sec. 4.4), in (view, row, col) order, into pool (device, cap
+ * entries).  n_pool (device, 2 x u32): [0] = entries written (<= cap), [1] =
+ * accepted pixels in all crops (larger than [0] if cap was too small).  The
+ * context keeps a scratch of one byte per image pixel of its views. */
+int snk_ray_pool(snk_ctx *ctx, const snk_window *win, const int32_t *view_rects, uint32_t *pool, int64_t cap,
+                 uint32_t *n_pool, snk_stream_t stream);
+/* A batch of B pixels drawn uniformly from the pool (device pool, n_pool as
+ * written by snk_ray_pool): pix[i] = pool[(x >> 8) * n_pool[0] >> 24], x =
+ * word i % 4 of Philox-4x32-10 with counter (i / 4, 0, 0, 0) and key (seed,
+ * iteration).  An empty pool gives pixels of no view, which a step rejects. */
+int snk_draw_batch(snk_ctx *ctx, const uint32_t *pool, const uint32_t *n_pool, int B, uint32_t seed,
+                   uint32_t iteration, uint32_t *pix, snk_stream_t stream);
+
 /* ---- tile residency (snake sweep, Sec. 4.4) ------------------------------ */
 
 /* Host only: bytes of one parked tile of `model`, a contiguous block laid out

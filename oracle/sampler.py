@@ -107,14 +107,20 @@ class Segments:
     ray_off: np.ndarray     # (B+1,) int64 CSR of samples per ray
 
 
-def segments(o, d, wf, K_ray, K_min, K_max):
-    """Acceptance test and segment split for every ray; see module docstring."""
-    B = o.shape[0]
+def accepted(o, d, wf):
+    """Sec. 4.4 acceptance of every ray: its scene-box interval is non-empty and lies
+    inside the window box.  Returns (ok, ts_in, ts_out, inv)."""
     zero3 = np.zeros(3, F32)
     ts_in, ts_out, inv = slab(o, d, wf.scene_lo, wf.scene_hi)
     tw_in, tw_out, _ = slab(o, d, zero3, wf.win_hi)
     hit = ts_in < ts_out
-    ok = hit & (tw_in <= ts_in) & (ts_out <= tw_out)
+    return hit & (tw_in <= ts_in) & (ts_out <= tw_out), ts_in, ts_out, inv
+
+
+def segments(o, d, wf, K_ray, K_min, K_max):
+    """Acceptance test and segment split for every ray; see module docstring."""
+    B = o.shape[0]
+    ok, ts_in, ts_out, inv = accepted(o, d, wf)
 
     n_seg = np.zeros(B, np.int64)
     slot = np.full((B, 3), 255, np.int64)

@@ -31,6 +31,8 @@ struct snk_ctx {
   uint32_t *amax = nullptr;    // [4] per-slot max |feature| (binary32 bits), E4M3 path
   snk::Tuning tune;            // launch shapes (snk_autotune / snk_set_tuning)
   bool tuned = false;
+  void *pool_ws = nullptr;     // ray pool scratch: base [kMaxViews + 1] i64 | chunk counts | pixel flags
+  size_t pool_ws_bytes = 0;
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -352,6 +354,7 @@ int snk_ctx_destroy(snk_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->pool_ws) cudaFree(ctx->pool_ws);
   if (ctx->d_views) cudaFree(ctx->d_views);
   if (ctx->h_views) cudaFreeHost(ctx->h_views);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -891,6 +894,71 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
   }
   ctx->tuned = true;
   if (out) to_abi(ctx->tune, true, out);
+  return SNK_OK;
+}
+
+int snk_build_crops(snk_ctx *ctx, const snk_window *win, int margin, int32_t *tile_rects, int32_t *view_rects,
+                    snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (!win) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
+  WinParams wp;
+  int rc = check_window(ctx, win, win->nx * win->ny, &wp);
+  if (rc) return rc;
+  if (!tile_rects || !view_rects || margin < 0 || margin > 4096)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_build_crops: NULL output or margin outside 0..4096");
+  if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
+  CropParams cp;
+  cp.tile[0] = win->tile_size[0];
+  cp.tile[1] = win->tile_size[1];
+  cp.margin = margin;
+  SNK_CK(ctx, launch_crops(ctx->d_views, ctx->n_views, wp, cp, tile_rects, view_rects, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_ray_pool(snk_ctx *ctx, const snk_window *win, const int32_t *view_rects, uint32_t *pool, int64_t cap,
+                 uint32_t *n_pool, snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (!win) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
+  WinParams wp;
+  int rc = check_window(ctx, win, win->nx * win->ny, &wp);
+  if (rc) return rc;
+  if (!view_rects || !pool || !n_pool || cap < 1 || cap > 0xFFFFFFFFll)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_ray_pool: NULL buffer or cap outside 1..2^32-1");
+  if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
+  // scratch sized by the views' whole images (an upper bound of any crop set)
+  int64_t max_pixels = 0;
+  for (int v = 0; v < ctx->n_views; ++v) max_pixels += (int64_t)ctx->h_views[v].width * ctx->h_views[v].height;
+  const int64_t nc = pool_chunks(max_pixels);
+  const size_t need = 256 * 16 + (size_t)nc * 4 + 256 + (size_t)max_pixels;
+  if (need > ctx->pool_ws_bytes) {
+    if (ctx->pool_ws) {
+      SNK_CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+      SNK_CK(ctx, cudaFree(ctx->pool_ws));
+      ctx->pool_ws = nullptr;
+      ctx->pool_ws_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->pool_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->pool_ws = nullptr;
+      return fail(ctx, SNK_ERR_OOM, "snk_ray_pool: scratch of %zu bytes could not be allocated", need);
+    }
+    ctx->pool_ws_bytes = need;
+  }
+  char *w = static_cast<char *>(ctx->pool_ws);
+  int64_t *base = reinterpret_cast<int64_t *>(w);
+  uint32_t *chunk = reinterpret_cast<uint32_t *>(w + 256 * 16);
+  uint8_t *flags = reinterpret_cast<uint8_t *>(w + 256 * 16 + ((size_t)nc * 4 + 255) / 256 * 256);
+  SNK_CK(ctx, launch_ray_pool(ctx->d_views, ctx->n_views, wp, view_rects, base, max_pixels, flags, chunk, pool, cap,
+                              n_pool, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_draw_batch(snk_ctx *ctx, const uint32_t *pool, const uint32_t *n_pool, int B, uint32_t seed, uint32_t iteration,
+                   uint32_t *pix, snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (!pool || !n_pool || !pix || B < 0 || B > (1 << 22))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_draw_batch: NULL buffer or B outside 0..2^22");
+  SNK_CK(ctx, launch_draw(pool, n_pool, B, seed, iteration, pix, (cudaStream_t)stream));
   return SNK_OK;
 }
 

@@ -77,6 +77,20 @@ cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st);
 // E4M3 path, first pass: binary32 features from the FP16 tables into feat32 and
 // the per-slot max |feature| into amax (which must be zero before the launch).
 cudaError_t launch_gather_amax(const FieldArgs &a, int sm_count, cudaStream_t st);
+// Crops and ray pool of a window (crops.cu).
+struct CropParams {
+  double tile[2];  // tile extent in x, y (metres)
+  int32_t margin;  // pixels added on every side of a tile's corner box
+};
+cudaError_t launch_crops(const DevView *views, int n_views, const WinParams &win, const CropParams &cp,
+                         int32_t *tile_rects, int32_t *view_rects, cudaStream_t st);
+int64_t pool_chunks(int64_t max_pixels);
+// n_pool[0] = pool entries written (<= cap), n_pool[1] = accepted pixels in all crops
+cudaError_t launch_ray_pool(const DevView *views, int n_views, const WinParams &win, const int32_t *view_rects,
+                            int64_t *base, int64_t max_pixels, uint8_t *flags, uint32_t *chunk_cnt, uint32_t *pool,
+                            int64_t cap, uint32_t *n_pool, cudaStream_t st);
+cudaError_t launch_draw(const uint32_t *pool, const uint32_t *n_pool, int B, uint32_t seed, uint32_t iteration,
+                        uint32_t *pix, cudaStream_t st);
 // codes[i] = E4M3(x[i] / scale), the conversion the E4M3 path uses.
 cudaError_t launch_quantize_e4m3(const float *x, int64_t n, float scale, uint8_t *codes, cudaStream_t st);
 

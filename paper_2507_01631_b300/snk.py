@@ -97,6 +97,9 @@ SIGNATURES = {
                            POINTER(SnkParams), _P, _P, _P]),
     "snk_sync_status": (c_int, [_P, _P, _P]),
     "snk_quantize_e4m3": (c_int, [_P, _P, c_int64, c_float, _P, _P]),
+    "snk_build_crops": (c_int, [_P, POINTER(SnkWindow), c_int, _P, _P, _P]),
+    "snk_ray_pool": (c_int, [_P, POINTER(SnkWindow), _P, _P, c_int64, _P, _P]),
+    "snk_draw_batch": (c_int, [_P, _P, _P, c_int, c_uint32, c_uint32, _P, _P]),
     "snk_tile_bytes": (c_int, [POINTER(SnkModel), POINTER(c_int64)]),
     "snk_tile_park": (c_int, [_P, POINTER(SnkModel), POINTER(SnkParams), c_int, _P, _P]),
     "snk_tile_unpark": (c_int, [_P, POINTER(SnkModel), POINTER(SnkParams), c_int, _P, _P]),
