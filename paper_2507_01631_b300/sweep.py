@@ -106,6 +106,7 @@ class SnakeSweep:
         slots = [self.slot_of[t] for t in window_members(pos)]
         return snk.window_struct(self.w.window(pos, slot=slots))
 
+
     def run(self, iters, batch_at, views_at=None, on_step=None):
         """Train `iters` steps at every position of the snake order.
         batch_at(pos, i) -> int32 device pixels; views_at(pos) (optional) sets the
@@ -176,6 +177,41 @@ class SnakeSweep:
                 int(tr.steps[0].item()))
 
 
+class DeviceBatches:
+    """Ray batches built on the device (Sec. 4.3 crops, Sec. 4.4 acceptance): per
+    window position the crops of its tiles in every view (snk_build_crops), the
+    accepted pixels of those crops (snk_ray_pool), then one Philox draw per step
+    (snk_draw_batch).  The views' resident crops follow the window: set_crops(rects)
+    receives the per-view rectangles (host) to load the matching target regions."""
+
+    def __init__(self, ctx, workload, n_views, rays, margin=64, cap=1 << 26, seed=1):
+        self.ctx, self.w, self.nv, self.rays, self.margin, self.cap, self.seed = ctx, workload, n_views, rays, margin, cap, seed
+        self.tile_rects = torch.zeros(n_views * 16, dtype=torch.int32, device="cuda")
+        self.view_rects = torch.zeros(n_views * 4, dtype=torch.int32, device="cuda")
+        self.pool = torch.zeros(cap, dtype=torch.int32, device="cuda")
+        self.n_pool = torch.zeros(2, dtype=torch.int32, device="cuda")
+        self.pix = torch.zeros(rays, dtype=torch.int32, device="cuda")
+        self.step = 0
+
+    def position(self, pos, set_crops=None):
+        """Crops and pool of the window at pos; returns the view rectangles (host)."""
+        ws = snk.window_struct(self.w.window(pos))
+        self.ctx.call("snk_build_crops", ctypes.byref(ws), self.margin, snk.ptr(self.tile_rects),
+                      snk.ptr(self.view_rects), None)
+        rects = self.view_rects.cpu().numpy().reshape(self.nv, 4)
+        if set_crops is not None:
+            set_crops(rects)
+        self.ctx.call("snk_ray_pool", ctypes.byref(ws), snk.ptr(self.view_rects), snk.ptr(self.pool), self.cap,
+                      snk.ptr(self.n_pool), None)
+        return rects
+
+    def draw(self):
+        self.ctx.call("snk_draw_batch", snk.ptr(self.pool), snk.ptr(self.n_pool), self.rays, self.seed, self.step,
+                      snk.ptr(self.pix), None)
+        self.step += 1
+        return self.pix
+
+
 def _main():
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from synth import workloads as W
@@ -185,6 +221,8 @@ def _main():
     ap.add_argument("--grid", type=int, nargs="+", default=[3, 4, 5])
     ap.add_argument("--iters", type=int, default=20, help="training steps per window position")
     ap.add_argument("--rays", type=int, default=0)
+    ap.add_argument("--device-batches", type=int, default=1,
+                    help="1: crops, ray pool and batches built on the device; 0: host-drawn batches")
     args = ap.parse_args()
     from . import build
     build.build()
@@ -213,7 +251,10 @@ def _main():
                               max(r[1] + r[3] for r in rs) - min(r[1] for r in rs)) for rs in rects]
         hmax = max(c[2] for cs in crops_at.values() for c in cs)
         wmax = max(c[3] for cs in crops_at.values() for c in cs)
-        img = torch.from_numpy(synth.smooth_images(w.seed + 17, 1, max(hmax, wmax), max(hmax, wmax))[0]).cuda()
+        side = max(hmax, wmax)
+        if args.device_batches:  # crops come from the device: an image-sized buffer bounds any of them
+            side = max(max(c.height, c.width) for c in cams)
+        img = torch.from_numpy(synth.smooth_images(w.seed + 17, 1, side, side)[0]).cuda()
         images = [img for _ in cams]
 
         def views_at(pos):
@@ -223,10 +264,26 @@ def _main():
                 cs.append(cam)
             ctx.set_views(cs, images)
 
-        batches = {pos: [torch.from_numpy(W.batch(w, cams, 50 + i, pos=pos).view(np.int32)).cuda() for i in range(2)]
-                   for pos in order}
-        t0 = time.perf_counter()
-        stats = sw.run(args.iters, lambda pos, i: batches[pos][i % 2], views_at=views_at)
+        if args.device_batches:
+            db = DeviceBatches(ctx, w, len(cams), w.n_rays, margin=w.crop_margin)
+            ctx.set_views(cams, images)  # whole-image crops for the first crop build
+
+            def views_at_dev(pos):
+                def set_crops(rects):
+                    cs = []
+                    for cam, r in zip(cams, rects):
+                        cam.crop = tuple(int(x) for x in r)
+                        cs.append(cam)
+                    ctx.set_views(cs, images)
+                db.position(pos, set_crops)
+
+            t0 = time.perf_counter()
+            stats = sw.run(args.iters, lambda pos, i: db.draw(), views_at=views_at_dev)
+        else:
+            batches = {pos: [torch.from_numpy(W.batch(w, cams, 50 + i, pos=pos).view(np.int32)).cuda()
+                             for i in range(2)] for pos in order}
+            t0 = time.perf_counter()
+            stats = sw.run(args.iters, lambda pos, i: batches[pos][i % 2], views_at=views_at)
         wall = time.perf_counter() - t0
         st = sw.tr.read_state()
         train = sum(s["train_ms"] for s in stats)
@@ -235,6 +292,7 @@ def _main():
                     "rays_per_iter": w.n_rays, "wall_s": wall, "train_ms": train, "move_ms_total": move,
                     "move_ms_per_move": move / max(len(order) - 1, 1), "ms_per_position": (train + move) / len(order),
                     "ms_per_tile": (train + move) / (g * g), "status": ctx.sync_status(sw.tr.state),
+                    "batches": "device (crops, ray pool, Philox draws)" if args.device_batches else "host",
                     "final_loss": st["loss"]})
         del sw
         torch.cuda.empty_cache()
