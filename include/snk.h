@@ -141,12 +141,22 @@ typedef struct {
 } snk_layout;
 
 /* Sampler: samples per segment K = clamp(rint(K_ray len_seg / len_ray),
- * K_min, K_max); render = 1 puts every sample at its bin centre. */
+ * K_min, K_max); render = 1 puts every sample at its bin centre.
+ * Occupancy culling (Sec. 4.1, SAT-NGP's coarse voxel grid): with occ_res > 0
+ * the K stratified candidates of a segment are placed as without culling and
+ * only those whose cell of the slot's grid is occupied become samples (each
+ * keeps its bin width as delta); seg_n then counts the kept samples.  The grid
+ * of slot k is occupancy[k * R^3 ...], cell (x, y, z) = min(floor(l R), R - 1)
+ * of the tile-local position l (binary32), stored at (z R + y) R + x; nonzero =
+ * occupied.  snk_occupancy_update maintains such a grid. */
 typedef struct {
     int32_t K_ray, K_min, K_max;
     int32_t render;
     uint32_t seed;
-    uint32_t iteration; /* Philox key word; the training step uses its own counter */
+    uint32_t iteration;       /* Philox key word; the training step uses its own counter */
+    int32_t occ_res;          /* cells per axis of each slot's occupancy grid; 0: no culling */
+    int32_t reserved;
+    const uint8_t *occupancy; /* device [n_slots][occ_res^3], or NULL when occ_res = 0 */
 } snk_sampler;
 
 /* Adam hyper-parameters (I-NGP's: 1e-2, 0.9, 0.99, 1e-15, 1e-6). */
@@ -347,6 +357,24 @@ int snk_ray_pool(snk_ctx *ctx, const snk_window *win, const int32_t *view_rects,
  * iteration).  An empty pool gives pixels of no view, which a step rejects. */
 int snk_draw_batch(snk_ctx *ctx, const uint32_t *pool, const uint32_t *n_pool, int B, uint32_t seed,
                    uint32_t iteration, uint32_t *pix, snk_stream_t stream);
+
+/* ---- occupancy grid (Sec. 4.1, SAT-NGP's coarse voxel grid) -------------- */
+
+/* Update the occupancy grids of all slots: every cell of slot k's R^3 grid
+ * gets sigma at one point p = (cell + u) x (1 / R) (binary32 per axis; u = three
+ * words of Philox-4x32-10 with counter (cell, k, 3, 0) and key (seed, step),
+ * each (w >> 8) 2^-24), evaluated with the slot's field of `model` and `p` (the
+ * kernels of a step, at the model's precision); then
+ *   density <- max(decay x density, sigma)
+ *   occupancy <- density > min(threshold, mean of slot k's density).
+ * density [n_slots][R^3] binary32 and occupancy [n_slots][R^3] u8 are caller-
+ * owned device arrays (cell (x, y, z) at (z R + y) R + x); start from density 0
+ * and occupancy 1 everywhere (no culling before the first update).  R a
+ * multiple of 8 in 8..512; uses the context's sample workspace for
+ * n_slots R^3 samples (may grow it).  The grid feeds snk_sampler.occupancy. */
+int snk_occupancy_update(snk_ctx *ctx, const snk_model *model, const snk_params *p, float *density,
+                         uint8_t *occupancy, int R, float decay, float threshold, uint32_t seed, uint32_t step,
+                         snk_stream_t stream);
 
 /* ---- tile residency (snake sweep, Sec. 4.4) ------------------------------ */
 

@@ -33,6 +33,8 @@ struct snk_ctx {
   bool tuned = false;
   void *pool_ws = nullptr;     // ray pool scratch: base [kMaxViews + 1] i64 | chunk counts | pixel flags
   size_t pool_ws_bytes = 0;
+  void *occ_ws = nullptr;      // occupancy update scratch: state | per-block partial sums | thresholds
+  size_t occ_ws_bytes = 0;
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -217,6 +219,10 @@ int check_sampler(snk_ctx *ctx, const snk_sampler *s, SamplerParams *o) {
   o->seed = s->seed;
   o->iteration = s->iteration;
   o->use_state_iteration = 0;
+  if (s->occ_res < 0 || s->occ_res > 1024 || (s->occ_res > 0) != (s->occupancy != nullptr))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "occupancy: need 1 <= occ_res <= 1024 with a grid, or occ_res 0 without");
+  o->occ_res = s->occ_res;
+  o->occ = s->occ_res > 0 ? s->occupancy : nullptr;
   return SNK_OK;
 }
 
@@ -237,6 +243,7 @@ size_t layout_ws(snk_ctx *ctx, char *base, int64_t B, int64_t S) {
   rb.seg_t = (float *)(base + carve(off, sizeof(float) * 6 * B));
   rb.seg_n = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 3 * B));
   rb.seg_off = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 3 * B));
+  rb.seg_k = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 3 * B));
   rb.cnt = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 5 * B));
   rb.excl = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 5 * B));
   rb.block_tot = (uint32_t *)(base + carve(off, sizeof(uint32_t) * 5 * nb));
@@ -355,6 +362,7 @@ int snk_ctx_destroy(snk_ctx *ctx) {
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->pool_ws) cudaFree(ctx->pool_ws);
+  if (ctx->occ_ws) cudaFree(ctx->occ_ws);
   if (ctx->d_views) cudaFree(ctx->d_views);
   if (ctx->h_views) cudaFreeHost(ctx->h_views);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -950,6 +958,47 @@ int snk_ray_pool(snk_ctx *ctx, const snk_window *win, const int32_t *view_rects,
   uint8_t *flags = reinterpret_cast<uint8_t *>(w + 256 * 16 + ((size_t)nc * 4 + 255) / 256 * 256);
   SNK_CK(ctx, launch_ray_pool(ctx->d_views, ctx->n_views, wp, view_rects, base, max_pixels, flags, chunk, pool, cap,
                               n_pool, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_occupancy_update(snk_ctx *ctx, const snk_model *model, const snk_params *p, float *density,
+                         uint8_t *occupancy, int R, float decay, float threshold, uint32_t seed, uint32_t step,
+                         snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  if ((rc = check_params(ctx, model, p, false))) return rc;
+  if (!density || !occupancy || R < 8 || R > 512 || R % 8 != 0)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_occupancy_update: NULL grid or R not a multiple of 8 in 8..512");
+  if (!(decay >= 0.0f && decay <= 1.0f) || !(threshold >= 0.0f) || !std::isfinite(threshold))
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_occupancy_update: need 0 <= decay <= 1 and a finite threshold >= 0");
+  const int64_t S = (int64_t)model->n_slots * R * R * R;
+  if ((rc = ensure_ws(ctx, ctx->cap_rays > 0 ? ctx->cap_rays : 1, S))) return rc;
+  const size_t need = 256 + sizeof(float) * (size_t)occ_partials(model->n_slots, R) + 256;
+  if (need > ctx->occ_ws_bytes) {
+    if (ctx->occ_ws) {
+      SNK_CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+      SNK_CK(ctx, cudaFree(ctx->occ_ws));
+      ctx->occ_ws = nullptr;
+      ctx->occ_ws_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->occ_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->occ_ws = nullptr;
+      return fail(ctx, SNK_ERR_OOM, "snk_occupancy_update: scratch of %zu bytes could not be allocated", need);
+    }
+    ctx->occ_ws_bytes = need;
+  }
+  snk_state *state = static_cast<snk_state *>(ctx->occ_ws);
+  float *partial = reinterpret_cast<float *>(static_cast<char *>(ctx->occ_ws) + 256);
+  float *thr = partial + occ_partials(model->n_slots, R);
+  const cudaStream_t st = (cudaStream_t)stream;
+  SNK_CK(ctx, cudaMemsetAsync(state, 0, sizeof(snk_state), st));
+  SNK_CK(ctx, launch_occ_points(model->n_slots, R, seed, step, ctx->rb.smp_xyz, state, st));
+  if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  SNK_CK(ctx, launch_occ_update(model->n_slots, R, ctx->sigma_rgb, decay, threshold, density, occupancy, partial, thr,
+                                st));
   return SNK_OK;
 }
 

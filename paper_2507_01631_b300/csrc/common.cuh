@@ -46,7 +46,10 @@ struct SamplerParams {
   int32_t K_ray, K_min, K_max, render;
   uint32_t seed, iteration;
   int32_t use_state_iteration;  // 1: the jitter key's second word is state->iteration
+  int32_t occ_res;              // occupancy culling: cells per axis (0: none)
+  const uint8_t *occ;           // [n_slots][occ_res^3] occupied flags, cell (x, y, z) at (z R + y) R + x
 };
+
 
 // Grid level table passed by value to kernels.
 struct GridParams {
@@ -90,6 +93,18 @@ __device__ __forceinline__ float jitter(uint32_t seed, uint32_t iteration, uint3
   const uint32_t lane = j & 3u;
   const uint32_t x = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
   return u32_to_unit(x);
+}
+
+// Occupancy cell of a tile-local point l in [0, 1]^3 (binary32: c = min(floor(l R), R - 1)).
+__device__ __forceinline__ uint32_t occ_cell(const float l[3], int R) {
+  uint32_t c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int v = (int)floorf(fmul(l[a], (float)R));
+    v = v < R - 1 ? v : R - 1;
+    c[a] = (uint32_t)(v > 0 ? v : 0);
+  }
+  return (c[2] * (uint32_t)R + c[1]) * (uint32_t)R + c[0];
 }
 
 // ---- NGP dense index / spatial hash ----------------------------------------

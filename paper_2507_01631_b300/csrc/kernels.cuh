@@ -24,6 +24,7 @@ struct RayBuffers {
   float *seg_t;        // [B][3][2]
   uint32_t *seg_n;     // [B][3]
   uint32_t *seg_off;   // [B][3]
+  uint32_t *seg_k;     // [B][3] stratified candidates per segment (occupancy culling), or null
   uint32_t *cnt;       // [5][B]  per-slot sample counts, row 4 = accepted flag
   uint32_t *excl;      // [5][B]  exclusive scans of cnt within a scan block
   uint32_t *block_tot; // [5][nb] scan block totals, then bases
@@ -91,6 +92,12 @@ cudaError_t launch_ray_pool(const DevView *views, int n_views, const WinParams &
                             int64_t cap, uint32_t *n_pool, cudaStream_t st);
 cudaError_t launch_draw(const uint32_t *pool, const uint32_t *n_pool, int B, uint32_t seed, uint32_t iteration,
                         uint32_t *pix, cudaStream_t st);
+// Occupancy grid update (occupancy.cu).
+cudaError_t launch_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, float *xyz, snk_state *state,
+                              cudaStream_t st);
+int64_t occ_partials(int n_slots, int R);
+cudaError_t launch_occ_update(int n_slots, int R, const float *sigma_rgb, float decay, float threshold,
+                              float *density, uint8_t *occ, float *partial, float *thr, cudaStream_t st);
 // codes[i] = E4M3(x[i] / scale), the conversion the E4M3 path uses.
 cudaError_t launch_quantize_e4m3(const float *x, int64_t n, float scale, uint8_t *codes, cudaStream_t st);
 

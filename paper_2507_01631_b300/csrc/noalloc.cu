@@ -78,6 +78,8 @@ extern "C" int snk_sample_segments_static(const snk_window *win, const snk_camer
   if (sampler->K_min < 1 || sampler->K_max < sampler->K_min || sampler->K_max > 4096 || sampler->K_ray < 1 ||
       sampler->K_ray > 4096)
     return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: bad K_ray / K_min / K_max");
+  if (sampler->occ_res != 0 || sampler->occupancy != nullptr)
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: no occupancy culling (no scratch for it)");
   for (int v = 0; v < n_views; ++v)
     if (cams[v].kind != SNK_CAM_AFFINE && cams[v].kind != SNK_CAM_RPC3)
       return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: unknown camera kind");
@@ -110,6 +112,8 @@ extern "C" int snk_sample_segments_static(const snk_window *win, const snk_camer
   sp.seed = sampler->seed;
   sp.iteration = sampler->iteration;
   sp.use_state_iteration = 0;
+  sp.occ_res = 0;
+  sp.occ = nullptr;
 
   std::lock_guard<std::mutex> lock(g_mutex);
   int dev = 0;

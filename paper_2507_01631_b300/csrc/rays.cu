@@ -200,12 +200,105 @@ __global__ void k_scan_top(uint32_t *__restrict__ block_tot, int nb, int n_slots
 }
 
 // Warp per ray: segment offsets, then t, delta and tile-local xyz of every sample.
+// Window-local lower corner of the tile of parameter slot k.
+__device__ __forceinline__ void tile_lo(const WinParams &win, int k, float lo[3]) {
+  int tile = 0;
+  for (int q = 0; q < win.nx * win.ny; ++q)
+    if (win.slot[q] == k) tile = q;
+  const int ix = tile % win.nx, iy = tile / win.nx;
+  lo[0] = ix ? win.split[0] : 0.0f;
+  lo[1] = iy ? win.split[1] : 0.0f;
+  lo[2] = 0.0f;
+}
+
+// Candidate i of a segment (bin width w from t0; jitter index j0 + i along the ray):
+// returns t and writes the tile-local position l in [0, 1]^3.
+__device__ __forceinline__ float candidate(const float o[3], const float d[3], const float lo[3], const WinParams &win,
+                                           const SamplerParams &smp, uint32_t iteration, uint32_t ray, uint32_t i,
+                                           uint32_t j0, float w, float t0, float l[3]) {
+  const float u = smp.render ? 0.5f : jitter(smp.seed, iteration, ray, j0 + i);
+  const float t = fadd(t0, fmul(fadd((float)i, u), w));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = fadd(o[a], fmul(t, d[a]));
+    const float v = fmul(fsub(p, lo[a]), win.inv_size[a]);
+    l[a] = fminf(fmaxf(v, 0.0f), 1.0f);
+  }
+  return t;
+}
+
+__device__ __forceinline__ bool occupied(const SamplerParams &smp, int slot, const float l[3]) {
+  if (!smp.occ) return true;
+  const size_t R3 = (size_t)smp.occ_res * smp.occ_res * smp.occ_res;
+  return smp.occ[(size_t)slot * R3 + occ_cell(l, smp.occ_res)] != 0;
+}
+
 __global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_od, const uint8_t *__restrict__ seg_slot,
                           const float *__restrict__ seg_t, const uint32_t *__restrict__ seg_n,
                           const uint32_t *__restrict__ excl, const uint32_t *__restrict__ block_tot, int nb, int B,
                           WinParams win, SamplerParams smp, const snk_state *__restrict__ state,
-                          uint32_t *__restrict__ seg_off, float *__restrict__ smp_t, float *__restrict__ smp_dt,
-                          float *__restrict__ smp_xyz) {
+                          const uint32_t *__restrict__ seg_k, uint32_t *__restrict__ seg_off,
+                          float *__restrict__ smp_t, float *__restrict__ smp_dt, float *__restrict__ smp_xyz) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int r = warp;
+  const uint32_t iteration = smp.use_state_iteration ? state->iteration : smp.iteration;
+  float o[3], d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o[a] = ray_od[(size_t)a * B + r];
+    d[a] = ray_od[(size_t)(3 + a) * B + r];
+  }
+  uint32_t j0 = 0;  // jitter index of the segment's first candidate along the ray
+  for (int s = 0; s < 3; ++s) {
+    const int k = seg_slot[(size_t)r * 3 + s];
+    const uint32_t n = seg_n[(size_t)r * 3 + s];                 // samples written
+    const uint32_t nk = smp.occ ? seg_k[(size_t)r * 3 + s] : n;  // stratified candidates
+    uint32_t off = 0;
+    const bool live = k < kMaxSlots && n > 0 && state->slot_count[k] > 0;
+    if (live) off = state->slot_base[k] + block_tot[(size_t)k * nb + r / kScanChunk] + excl[(size_t)k * B + r];
+    if (lane == 0) seg_off[(size_t)r * 3 + s] = off;
+    if (!live) {
+      j0 += nk;
+      continue;
+    }
+    const float t0 = seg_t[((size_t)r * 3 + s) * 2 + 0], t1 = seg_t[((size_t)r * 3 + s) * 2 + 1];
+    const float w = fdiv(fsub(t1, t0), (float)nk);
+    float lo[3];
+    tile_lo(win, k, lo);
+    // the candidates in order; with culling only the occupied ones, compacted in order
+    uint32_t written = 0;
+    for (uint32_t i0 = 0; i0 < nk; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      float t = 0.f, l[3] = {0.f, 0.f, 0.f};
+      bool keep = false;
+      if (i < nk) {
+        t = candidate(o, d, lo, win, smp, iteration, (uint32_t)r, i, j0, w, t0, l);
+        keep = occupied(smp, k, l);
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const size_t q = (size_t)off + written + __popc(m & ((1u << lane) - 1u));
+        smp_t[q] = t;
+        smp_dt[q] = w;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) smp_xyz[q * 3 + a] = l[a];
+      }
+      written += __popc(m);
+    }
+    j0 += nk;
+  }
+}
+
+// Occupancy culling, count pass (warp per ray; Sec. 4.1, the SAT-NGP coarse voxel grid): the
+// stratified candidates of every segment are recomputed exactly as k_samples will place them and
+// kept if their cell is occupied.  seg_k <- candidates, seg_n <- kept, cnt rows <- kept per slot.
+__global__ void __launch_bounds__(512) k_cull_count(const float *__restrict__ ray_od, const uint8_t *__restrict__ seg_slot,
+                                                    const float *__restrict__ seg_t, uint32_t *__restrict__ seg_n,
+                                                    uint32_t *__restrict__ seg_k, uint32_t *__restrict__ cnt, int B,
+                                                    WinParams win, SamplerParams smp,
+                                                    const snk_state *__restrict__ state) {
   const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= B) return;
@@ -218,37 +311,36 @@ __global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_o
     d[a] = ray_od[(size_t)(3 + a) * B + r];
   }
   uint32_t j0 = 0;
+  uint32_t c[kMaxSlots] = {0u, 0u, 0u, 0u};
   for (int s = 0; s < 3; ++s) {
     const int k = seg_slot[(size_t)r * 3 + s];
-    const uint32_t n = seg_n[(size_t)r * 3 + s];
-    uint32_t off = 0;
-    const bool live = k < kMaxSlots && n > 0 && state->slot_count[k] > 0;
-    if (live) off = state->slot_base[k] + block_tot[(size_t)k * nb + r / kScanChunk] + excl[(size_t)k * B + r];
-    if (lane == 0) seg_off[(size_t)r * 3 + s] = off;
-    if (!live) continue;
-    int tile = 0;
-    for (int q = 0; q < win.nx * win.ny; ++q)
-      if (win.slot[q] == k) tile = q;
-    const int ix = tile % win.nx, iy = tile / win.nx;
-    const float lo[3] = {ix ? win.split[0] : 0.0f, iy ? win.split[1] : 0.0f, 0.0f};
-    const float t0 = seg_t[((size_t)r * 3 + s) * 2 + 0], t1 = seg_t[((size_t)r * 3 + s) * 2 + 1];
-    const float w = fdiv(fsub(t1, t0), (float)n);
-    for (uint32_t i = lane; i < n; i += 32) {
-      const float u = smp.render ? 0.5f : jitter(smp.seed, iteration, (uint32_t)r, j0 + i);
-      const float t = fadd(t0, fmul(fadd((float)i, u), w));
-      const size_t q = (size_t)off + i;
-      smp_t[q] = t;
-      smp_dt[q] = w;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float p = fadd(o[a], fmul(t, d[a]));
-        float l = fmul(fsub(p, lo[a]), win.inv_size[a]);
-        l = fminf(fmaxf(l, 0.0f), 1.0f);
-        smp_xyz[q * 3 + a] = l;
+    const uint32_t nk = seg_n[(size_t)r * 3 + s];
+    uint32_t kept = 0;
+    if (k < kMaxSlots && nk > 0) {
+      const float t0 = seg_t[((size_t)r * 3 + s) * 2 + 0], t1 = seg_t[((size_t)r * 3 + s) * 2 + 1];
+      const float w = fdiv(fsub(t1, t0), (float)nk);
+      float lo[3];
+      tile_lo(win, k, lo);
+      for (uint32_t i0 = 0; i0 < nk; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        bool keep = false;
+        if (i < nk) {
+          float l[3];
+          candidate(o, d, lo, win, smp, iteration, (uint32_t)r, i, j0, w, t0, l);
+          keep = occupied(smp, k, l);
+        }
+        kept += __popc(__ballot_sync(0xffffffffu, keep));
       }
+      c[k] += kept;
     }
-    j0 += n;
+    j0 += nk;
+    if (lane == 0) {
+      seg_k[(size_t)r * 3 + s] = nk;
+      seg_n[(size_t)r * 3 + s] = kept;
+    }
   }
+  if (lane == 0)
+    for (int k = 0; k < win.n_slots; ++k) cnt[(size_t)k * B + r] = c[k];
 }
 
 // ---- host launcher -------------------------------------------------------------
@@ -261,14 +353,20 @@ cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinP
   const int nt = tu.sampler_threads;
   k_rays<<<(B + nt - 1) / nt, nt, 0, st>>>(views, n_views, win, smp, pix, B, need_targets, rb.ray_od, rb.ray_ok,
                                           rb.seg_slot, rb.seg_t, rb.seg_n, rb.cnt, state);
+  if (smp.occ) {
+    if (!rb.seg_k) return cudaErrorInvalidValue;
+    k_cull_count<<<(unsigned)(((int64_t)B * 32 + nt - 1) / nt), nt, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n,
+                                                                           rb.seg_k, rb.cnt, B, win, smp, state);
+    count_launches(1);
+  }
   const int nb = scan_blocks(B);
   const dim3 g(nb, win.n_slots + 1);
   k_scan_local<<<g, kScanThreads, 0, st>>>(rb.cnt, B, win.n_slots, rb.excl, rb.block_tot);
   k_scan_top<<<1, 32 * (kMaxSlots + 1), 0, st>>>(rb.block_tot, nb, win.n_slots, cap, state);
   const int64_t threads = (int64_t)B * 32;
   k_samples<<<(unsigned)((threads + nt - 1) / nt), nt, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n, rb.excl,
-                                                                rb.block_tot, nb, B, win, smp, state, rb.seg_off,
-                                                                rb.smp_t, rb.smp_dt, rb.smp_xyz);
+                                                                rb.block_tot, nb, B, win, smp, state, rb.seg_k,
+                                                                rb.seg_off, rb.smp_t, rb.smp_dt, rb.smp_xyz);
   count_launches(4);
   return cudaGetLastError();
 }

@@ -45,7 +45,8 @@ class SnkLayout(Structure):
 
 class SnkSampler(Structure):
     _fields_ = [("K_ray", c_int32), ("K_min", c_int32), ("K_max", c_int32), ("render", c_int32),
-                ("seed", c_uint32), ("iteration", c_uint32)]
+                ("seed", c_uint32), ("iteration", c_uint32), ("occ_res", c_int32), ("reserved", c_int32),
+                ("occupancy", c_void_p)]
 
 
 class SnkAdam(Structure):
@@ -100,6 +101,8 @@ SIGNATURES = {
     "snk_build_crops": (c_int, [_P, POINTER(SnkWindow), c_int, _P, _P, _P]),
     "snk_ray_pool": (c_int, [_P, POINTER(SnkWindow), _P, _P, c_int64, _P, _P]),
     "snk_draw_batch": (c_int, [_P, _P, _P, c_int, c_uint32, c_uint32, _P, _P]),
+    "snk_occupancy_update": (c_int, [_P, POINTER(SnkModel), POINTER(SnkParams), _P, _P, c_int, c_float, c_float,
+                                     c_uint32, c_uint32, _P]),
     "snk_tile_bytes": (c_int, [POINTER(SnkModel), POINTER(c_int64)]),
     "snk_tile_park": (c_int, [_P, POINTER(SnkModel), POINTER(SnkParams), c_int, _P, _P]),
     "snk_tile_unpark": (c_int, [_P, POINTER(SnkModel), POINTER(SnkParams), c_int, _P, _P]),
@@ -200,8 +203,11 @@ def model_struct(L, F, log2_T, n_min, n_max, geo_out, colour, shared_colour, n_s
     return SnkModel(L, F, log2_T, n_min, n_max, hidden, geo_out, int(colour), int(shared_colour), n_slots, precision)
 
 
-def sampler_struct(K_ray, K_min, K_max, render=0, seed=0, iteration=0):
-    return SnkSampler(K_ray, K_min, K_max, render, seed & 0xFFFFFFFF, iteration & 0xFFFFFFFF)
+def sampler_struct(K_ray, K_min, K_max, render=0, seed=0, iteration=0, occupancy=None, occ_res=0):
+    """occupancy: device uint8 tensor [n_slots][occ_res^3] of occupied flags (culling), or None.
+    The struct keeps the tensor's address only: the caller keeps the tensor alive while it is used."""
+    return SnkSampler(K_ray, K_min, K_max, render, seed & 0xFFFFFFFF, iteration & 0xFFFFFFFF,
+                      occ_res if occupancy is not None else 0, 0, ptr(occupancy))
 
 
 def adam_struct(lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, l2_mlp=1e-6):
