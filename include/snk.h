@@ -140,6 +140,22 @@ typedef struct {
     int32_t n_colour_blocks;
 } snk_layout;
 
+/* Sampler modes.
+ *  SNK_SAMPLE_SEGMENTS (the paper's segmented sampler, Sec. 4.5): each segment
+ *    of a ray gets K = clamp(rint(K_ray len_seg / len_ray), K_min, K_max) bins
+ *    of width w = len_seg / K and a sample at t0 + (k + u) w, delta = w.
+ *  SNK_SAMPLE_UNIFORM (the NeRF-XL distribution the paper compares against):
+ *    K_ray bins over the ray's whole scene interval, sample j at
+ *    t_in + (j + u) w; each sample belongs to the tile holding its point and
+ *    the samples of a tile form its segment (seg_t = the ray's [t_in, t_out]);
+ *    delta = w.
+ *  SNK_SAMPLE_POINTS (point samples, the variant of the paper's remark on the
+ *    face point): K points per segment at t0 + k (len_seg / (K - 1)), the last
+ *    exactly at t1, and delta_i = t_i - t_{i-1} along the ray (0 for the
+ *    ray's first point): the face point of two segments is sampled twice and
+ *    the second copy has delta 0.  Needs K_min >= 2; no jitter. */
+enum { SNK_SAMPLE_SEGMENTS = 0, SNK_SAMPLE_UNIFORM = 1, SNK_SAMPLE_POINTS = 2 };
+
 /* Sampler: samples per segment K = clamp(rint(K_ray len_seg / len_ray),
  * K_min, K_max); render = 1 puts every sample at its bin centre.
  * Occupancy culling (Sec. 4.1, SAT-NGP's coarse voxel grid): with occ_res > 0
@@ -155,7 +171,7 @@ typedef struct {
     uint32_t seed;
     uint32_t iteration;       /* Philox key word; the training step uses its own counter */
     int32_t occ_res;          /* cells per axis of each slot's occupancy grid; 0: no culling */
-    int32_t reserved;
+    int32_t mode;             /* SNK_SAMPLE_SEGMENTS (default), _UNIFORM or _POINTS; culling needs _SEGMENTS */
     const uint8_t *occupancy; /* device [n_slots][occ_res^3], or NULL when occ_res = 0 */
 } snk_sampler;
 

@@ -24,11 +24,24 @@ Readings where the paper is silent (each listed in the design notes):
   With this convention the deltas of a ray add up to its box-intersection
   length and the face point gets no double weight.
 
+Two variants for comparisons (sampler modes):
+* UNIFORM, the NeRF-XL distribution the paper contrasts with its own (Sec.
+  4.5): K_ray bins over the whole scene interval [t_in, t_out], sample j at
+  t_in + (j + u_j) w; each sample belongs to the tile holding its point (a
+  point on an interior plane goes to the lower tile) and the samples of a tile
+  form its segment; delta = w.
+* POINTS, point samples (the setting of the paper's remark that the face
+  point, sampled as F_1 and again as N_2, has its N_2 density ignored): K
+  points per segment at t0 + k (t1 - t0) / (K - 1), the last exactly at t1,
+  with delta_i = t_i - t_{i-1} along the ray (0 for the ray's first point).
+
 Every float that decides something discrete (the slab parameters, the
 segment bounds, K, sample positions and local coordinates) is *defined* as
 the binary32 operation sequence written below (each numpy float32 op rounds
 once, no fused multiply-add).
 """
+
+SEGMENTS, UNIFORM, POINTS = 0, 1, 2
 from dataclasses import dataclass
 import numpy as np
 
@@ -165,6 +178,47 @@ def segments(o, d, wf, K_ray, K_min, K_max):
                     n_seg, slot, t0, t1, K, ray_off)
 
 
+def _uniform_t(a, w, seed, iteration, rid, j, render):
+    """t of sample j of a ray in the NeRF-XL distribution (binary32)."""
+    j = np.asarray(j)
+    u = np.full(j.shape, F32(0.5), F32) if render else philox.jitter(seed, iteration, rid, j).astype(F32)
+    return (a + ((j.astype(F32) + u).astype(F32) * w).astype(F32)).astype(F32)
+
+
+def segments_uniform(o, d, wf, K_ray, seed, iteration, render=False, ray_ids=None):
+    """NeRF-XL distribution: the segments are the runs of same-tile samples (see
+    module docstring); each segment's (t0, t1) is the ray's (t_in, t_out)."""
+    B = o.shape[0]
+    ok, ts_in, ts_out, inv = accepted(o, d, wf)
+    n_seg = np.zeros(B, np.int64)
+    slot = np.full((B, 3), 255, np.int64)
+    t0 = np.zeros((B, 3), F32)
+    t1 = np.zeros((B, 3), F32)
+    K = np.zeros((B, 3), np.int64)
+    for i in range(B):
+        if not ok[i]:
+            continue
+        a, b = ts_in[i], ts_out[i]
+        w = F32(F32(b - a) / F32(K_ray))
+        rid = i if ray_ids is None else int(ray_ids[i])
+        t = _uniform_t(a, w, seed, iteration, rid, np.arange(K_ray), render)
+        ix = (wf.nx == 2) & ((o[i, 0] + (t * d[i, 0]).astype(F32)).astype(F32) > wf.split[0])
+        iy = (wf.ny == 2) & ((o[i, 1] + (t * d[i, 1]).astype(F32)).astype(F32) > wf.split[1])
+        tile = iy.astype(np.int64) * wf.nx + ix.astype(np.int64)
+        s = -1
+        for j in range(K_ray):
+            if j == 0 or tile[j] != tile[j - 1]:
+                s += 1
+                slot[i, s] = wf.slot[tile[j]]
+                t0[i, s], t1[i, s] = a, b
+            K[i, s] += 1
+        n_seg[i] = s + 1
+    ray_off = np.zeros(B + 1, np.int64)
+    ray_off[1:] = np.cumsum(K.sum(axis=1))
+    return Segments(ok.astype(np.uint8), np.where(ok, ts_in, F32(0)), np.where(ok, ts_out, F32(0)),
+                    n_seg, slot, t0, t1, K, ray_off)
+
+
 @dataclass
 class Samples:
     ray: np.ndarray     # (S,) int64 ray index of each sample
@@ -174,7 +228,7 @@ class Samples:
     xyz: np.ndarray     # (S, 3) float32 tile-local coordinates in [0, 1]
 
 
-def stratified(o, d, seg, wf, seed, iteration, render=False, ray_ids=None):
+def stratified(o, d, seg, wf, seed, iteration, render=False, ray_ids=None, mode=SEGMENTS):
     """Sample positions of every segment (see module docstring).  `ray_ids`
     gives each ray's index in its batch (the jitter counter); default 0..B-1.
     Sample k of a segment [t0, t1] with K bins of width w = (t1 - t0) / K sits
@@ -185,17 +239,31 @@ def stratified(o, d, seg, wf, seed, iteration, render=False, ray_ids=None):
     B = o.shape[0]
     for i in range(B):
         j0 = 0
+        t_last = None
         for s in range(seg.n_seg[i]):
             k_n = int(seg.K[i, s])
             a, b = seg.t0[i, s], seg.t1[i, s]
-            w = F32(F32(b - a) / F32(k_n))
             k = np.arange(k_n)
-            if render:
-                u = np.full(k_n, F32(0.5), F32)
+            rid = i if ray_ids is None else int(ray_ids[i])
+            if mode == UNIFORM:
+                w = F32(F32(b - a) / F32(sum(int(x) for x in seg.K[i])))
+                t = _uniform_t(a, w, seed, iteration, rid, j0 + k, render)
+                dt = np.full(k_n, w, F32)
+            elif mode == POINTS:
+                w = F32(F32(b - a) / F32(k_n - 1))
+                t = (a + (k.astype(F32) * w).astype(F32)).astype(F32)
+                t[-1] = b
+                prev = np.concatenate([[t[0] if t_last is None else t_last], t[:-1]]).astype(F32)
+                dt = (t - prev).astype(F32)
+                t_last = b
             else:
-                rid = i if ray_ids is None else int(ray_ids[i])
-                u = philox.jitter(seed, iteration, rid, j0 + k).astype(F32)
-            t = (a + ((k.astype(F32) + u).astype(F32) * w).astype(F32)).astype(F32)
+                w = F32(F32(b - a) / F32(k_n))
+                if render:
+                    u = np.full(k_n, F32(0.5), F32)
+                else:
+                    u = philox.jitter(seed, iteration, rid, j0 + k).astype(F32)
+                t = (a + ((k.astype(F32) + u).astype(F32) * w).astype(F32)).astype(F32)
+                dt = np.full(k_n, w, F32)
             sl = int(seg.slot[i, s])
             tile = wf.slot.index(sl)
             ix, iy = tile % wf.nx, tile // wf.nx
@@ -208,7 +276,7 @@ def stratified(o, d, seg, wf, seed, iteration, render=False, ray_ids=None):
             rays_l.append(np.full(k_n, i))
             slot_l.append(np.full(k_n, sl))
             t_l.append(t)
-            dt_l.append(np.full(k_n, w, F32))
+            dt_l.append(dt)
             xyz_l.append(loc)
             j0 += k_n
     if not rays_l:

@@ -126,12 +126,16 @@ class StepResult:
     extra: dict = field(default_factory=dict)
 
 
-def sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids=None, occ=None):
-    """occ: (occupied flags (n_slots, R^3), R) to cull samples in empty cells, or None."""
+def sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids=None, occ=None, mode=0):
+    """occ: (occupied flags (n_slots, R^3), R) to cull samples in empty cells, or None;
+    mode: sampler.SEGMENTS (the paper's), UNIFORM (NeRF-XL) or POINTS."""
     o, d = camera.rays(cameras, pix, win.origin, win.origin[2], win.origin[2] + win.tile_size[2])
     wf = sampler.window_f32(win)
-    seg = sampler.segments(o, d, wf, cfg.K_ray, cfg.K_min, cfg.K_max)
-    smp = sampler.stratified(o, d, seg, wf, seed, iteration, render=render_mode, ray_ids=ray_ids)
+    if mode == sampler.UNIFORM:
+        seg = sampler.segments_uniform(o, d, wf, cfg.K_ray, seed, iteration, render=render_mode, ray_ids=ray_ids)
+    else:
+        seg = sampler.segments(o, d, wf, cfg.K_ray, cfg.K_min, cfg.K_max)
+    smp = sampler.stratified(o, d, seg, wf, seed, iteration, render=render_mode, ray_ids=ray_ids, mode=mode)
     if occ is not None:
         seg, smp = occupancy.cull(seg, smp, occ[0], occ[1])
     return o, d, seg, smp
@@ -170,12 +174,13 @@ def field_forward(cfg, flat, smp):
     return sigma, rgb, saved
 
 
-def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, seed, iteration, lr=None, occ=None):
+def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, seed, iteration, lr=None, occ=None,
+               mode=0):
     """One training step.  targets: list of per-view crop images (h, w, 3).
     steps: per-optimiser Adam step counts before this step (updated copy is
     returned in extra["steps"]).  lr: Adam learning rate (I-NGP's 1e-2 unless given).
     occ: (occupied flags, R) of the slots' occupancy grids to cull samples, or None."""
-    o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, False, occ=occ)
+    o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, False, occ=occ, mode=mode)
     sigma, rgb_s, saved = field_forward(cfg, flat, smp)
     rgb, depth, opac, tfin, _ = render.composite(sigma, rgb_s, smp.t.astype(np.float64),
                                                  smp.dt.astype(np.float64), seg.ray_off)
@@ -214,10 +219,11 @@ def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, s
     return res
 
 
-def render_rays(cfg, flat, cameras, win, pix, seed=0, iteration=0, render_mode=True, ray_ids=None, occ=None):
+def render_rays(cfg, flat, cameras, win, pix, seed=0, iteration=0, render_mode=True, ray_ids=None, occ=None,
+                mode=0):
     """Forward only: per-ray rgb, depth, opacity (bin-centre samples unless
     render_mode is False, then the training jitter of the given ray ids)."""
-    o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids, occ=occ)
+    o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids, occ=occ, mode=mode)
     sigma, rgb_s, _ = field_forward(cfg, flat, smp)
     rgb, depth, opac, tfin, _ = render.composite(sigma, rgb_s, smp.t.astype(np.float64),
                                                  smp.dt.astype(np.float64), seg.ray_off)

@@ -223,6 +223,13 @@ int check_sampler(snk_ctx *ctx, const snk_sampler *s, SamplerParams *o) {
     return fail(ctx, SNK_ERR_INVALID_ARG, "occupancy: need 1 <= occ_res <= 1024 with a grid, or occ_res 0 without");
   o->occ_res = s->occ_res;
   o->occ = s->occ_res > 0 ? s->occupancy : nullptr;
+  if (s->mode != SNK_SAMPLE_SEGMENTS && s->mode != SNK_SAMPLE_UNIFORM && s->mode != SNK_SAMPLE_POINTS)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "sampler mode must be SNK_SAMPLE_SEGMENTS, _UNIFORM or _POINTS");
+  if (s->mode != SNK_SAMPLE_SEGMENTS && s->occ_res > 0)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "occupancy culling needs SNK_SAMPLE_SEGMENTS");
+  if (s->mode == SNK_SAMPLE_POINTS && s->K_min < 2)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "SNK_SAMPLE_POINTS needs K_min >= 2 (both segment ends)");
+  o->mode = s->mode;
   return SNK_OK;
 }
 

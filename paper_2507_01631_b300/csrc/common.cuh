@@ -48,7 +48,12 @@ struct SamplerParams {
   int32_t use_state_iteration;  // 1: the jitter key's second word is state->iteration
   int32_t occ_res;              // occupancy culling: cells per axis (0: none)
   const uint8_t *occ;           // [n_slots][occ_res^3] occupied flags, cell (x, y, z) at (z R + y) R + x
+  int32_t mode;                 // kSampleSegments, kSampleUniform or kSamplePoints
 };
+// Sampler modes: the segmented sampler (Sec. 4.5; K bins per segment, delta = bin width); the
+// NeRF-XL distribution the paper compares against (K_ray bins over the whole ray, each sample in
+// the tile holding its point); point samples with both segment ends and delta_i = t_i - t_{i-1}.
+constexpr int kSampleSegments = 0, kSampleUniform = 1, kSamplePoints = 2;
 
 
 // Grid level table passed by value to kernels.

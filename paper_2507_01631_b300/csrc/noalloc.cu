@@ -114,6 +114,10 @@ extern "C" int snk_sample_segments_static(const snk_window *win, const snk_camer
   sp.use_state_iteration = 0;
   sp.occ_res = 0;
   sp.occ = nullptr;
+  if (sampler->mode < SNK_SAMPLE_SEGMENTS || sampler->mode > SNK_SAMPLE_POINTS ||
+      (sampler->mode == SNK_SAMPLE_POINTS && sampler->K_min < 2))
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: bad sampler mode");
+  sp.mode = sampler->mode;
 
   std::lock_guard<std::mutex> lock(g_mutex);
   int dev = 0;

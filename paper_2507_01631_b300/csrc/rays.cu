@@ -14,6 +14,20 @@
 
 namespace snk {
 
+// NeRF-XL mode: sample j of the ray at t = t_in + (j + u) w (u = 0.5 when rendering).
+__device__ __forceinline__ float uniform_t(float t_in, float w, const SamplerParams &smp, uint32_t iteration,
+                                           uint32_t ray, uint32_t j) {
+  const float u = smp.render ? 0.5f : jitter(smp.seed, iteration, ray, j);
+  return fadd(t_in, fmul(fadd((float)j, u), w));
+}
+
+// Window tile (iy nx + ix) holding the point at t (a point on an interior plane goes to the lower tile).
+__device__ __forceinline__ int point_tile(const float o[3], const float d[3], float t, const WinParams &win) {
+  const int ix = (win.nx == 2 && fadd(o[0], fmul(t, d[0])) > win.split[0]) ? 1 : 0;
+  const int iy = (win.ny == 2 && fadd(o[1], fmul(t, d[1])) > win.split[1]) ? 1 : 0;
+  return iy * win.nx + ix;
+}
+
 // One thread per ray: camera -> (o, d) -> acceptance -> <= 3 segments -> K per segment.
 __global__ void __launch_bounds__(512) k_rays(const DevView *__restrict__ views, int n_views, WinParams win, SamplerParams smp,
                        const uint32_t *__restrict__ pix, int B, int need_targets, float *__restrict__ ray_od,
@@ -50,7 +64,26 @@ __global__ void __launch_bounds__(512) k_rays(const DevView *__restrict__ views,
   uint8_t s_slot[3] = {255, 255, 255};
   float s_t0[3] = {0.f, 0.f, 0.f}, s_t1[3] = {0.f, 0.f, 0.f};
   uint32_t s_n[3] = {0u, 0u, 0u};
-  if (ok) {
+  if (ok && smp.mode == kSampleUniform) {
+    // K_ray bins over the whole scene interval; each sample belongs to the tile holding its point,
+    // the samples of a tile are one run along the ray (x(t), y(t) are monotone) and one segment
+    const float a = sc.t_in, b = sc.t_out;
+    const uint32_t iteration = smp.use_state_iteration ? state->iteration : smp.iteration;
+    const float w = fdiv(fsub(b, a), (float)smp.K_ray);
+    int ns = -1, last = -1;
+    for (int j = 0; j < smp.K_ray; ++j) {
+      const float t = uniform_t(a, w, smp, iteration, (uint32_t)r, (uint32_t)j);
+      const int tile = point_tile(o, d, t, win);
+      if (tile != last) {
+        if (++ns == 3) break;  // cannot happen: at most two interior planes are crossed
+        last = tile;
+        s_slot[ns] = (uint8_t)win.slot[tile];
+        s_t0[ns] = a;
+        s_t1[ns] = b;
+      }
+      s_n[ns] += 1u;
+    }
+  } else if (ok) {
     const float a = sc.t_in, b = sc.t_out;
     float cut[2] = {0.f, 0.f};
     int nc = 0;
@@ -211,6 +244,17 @@ __device__ __forceinline__ void tile_lo(const WinParams &win, int k, float lo[3]
   lo[2] = 0.0f;
 }
 
+// Tile-local position in [0, 1]^3 of the point at t.
+__device__ __forceinline__ void tile_local(const float o[3], const float d[3], float t, const float lo[3],
+                                           const WinParams &win, float l[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = fadd(o[a], fmul(t, d[a]));
+    const float v = fmul(fsub(p, lo[a]), win.inv_size[a]);
+    l[a] = fminf(fmaxf(v, 0.0f), 1.0f);
+  }
+}
+
 // Candidate i of a segment (bin width w from t0; jitter index j0 + i along the ray):
 // returns t and writes the tile-local position l in [0, 1]^3.
 __device__ __forceinline__ float candidate(const float o[3], const float d[3], const float lo[3], const WinParams &win,
@@ -218,12 +262,7 @@ __device__ __forceinline__ float candidate(const float o[3], const float d[3], c
                                            uint32_t j0, float w, float t0, float l[3]) {
   const float u = smp.render ? 0.5f : jitter(smp.seed, iteration, ray, j0 + i);
   const float t = fadd(t0, fmul(fadd((float)i, u), w));
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float p = fadd(o[a], fmul(t, d[a]));
-    const float v = fmul(fsub(p, lo[a]), win.inv_size[a]);
-    l[a] = fminf(fmaxf(v, 0.0f), 1.0f);
-  }
+  tile_local(o, d, t, lo, win, l);
   return t;
 }
 
@@ -250,7 +289,8 @@ __global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_o
     o[a] = ray_od[(size_t)a * B + r];
     d[a] = ray_od[(size_t)(3 + a) * B + r];
   }
-  uint32_t j0 = 0;  // jitter index of the segment's first candidate along the ray
+  uint32_t j0 = 0;         // jitter index of the segment's first candidate along the ray
+  float t_last = __int_as_float(0x7fffffff);  // points mode: t of the ray's previous sample (NaN: none)
   for (int s = 0; s < 3; ++s) {
     const int k = seg_slot[(size_t)r * 3 + s];
     const uint32_t n = seg_n[(size_t)r * 3 + s];                 // samples written
@@ -264,29 +304,43 @@ __global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_o
       continue;
     }
     const float t0 = seg_t[((size_t)r * 3 + s) * 2 + 0], t1 = seg_t[((size_t)r * 3 + s) * 2 + 1];
-    const float w = fdiv(fsub(t1, t0), (float)nk);
+    // bin width: K bins per segment, K_ray bins over the ray (NeRF-XL), or K - 1 gaps (points)
+    const float w = smp.mode == kSampleUniform ? fdiv(fsub(t1, t0), (float)smp.K_ray)
+                    : smp.mode == kSamplePoints ? fdiv(fsub(t1, t0), (float)(nk - 1))
+                                                : fdiv(fsub(t1, t0), (float)nk);
     float lo[3];
     tile_lo(win, k, lo);
     // the candidates in order; with culling only the occupied ones, compacted in order
     uint32_t written = 0;
     for (uint32_t i0 = 0; i0 < nk; i0 += 32) {
       const uint32_t i = i0 + lane;
-      float t = 0.f, l[3] = {0.f, 0.f, 0.f};
+      float t = 0.f, dt = w, l[3] = {0.f, 0.f, 0.f};
       bool keep = false;
       if (i < nk) {
-        t = candidate(o, d, lo, win, smp, iteration, (uint32_t)r, i, j0, w, t0, l);
+        if (smp.mode == kSampleSegments) {
+          t = candidate(o, d, lo, win, smp, iteration, (uint32_t)r, i, j0, w, t0, l);
+        } else if (smp.mode == kSampleUniform) {
+          t = uniform_t(t0, w, smp, iteration, (uint32_t)r, j0 + i);
+          tile_local(o, d, t, lo, win, l);
+        } else {
+          t = i + 1 == nk ? t1 : fadd(t0, fmul((float)i, w));
+          const float tp = i == 0 ? (t_last == t_last ? t_last : t) : fadd(t0, fmul((float)(i - 1), w));
+          dt = fsub(t, tp);
+          tile_local(o, d, t, lo, win, l);
+        }
         keep = occupied(smp, k, l);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, keep);
       if (keep) {
         const size_t q = (size_t)off + written + __popc(m & ((1u << lane) - 1u));
         smp_t[q] = t;
-        smp_dt[q] = w;
+        smp_dt[q] = dt;
 #pragma unroll
         for (int a = 0; a < 3; ++a) smp_xyz[q * 3 + a] = l[a];
       }
       written += __popc(m);
     }
+    if (smp.mode == kSamplePoints) t_last = t1;  // the segment's last point
     j0 += nk;
   }
 }

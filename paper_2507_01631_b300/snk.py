@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libsnk.so")
 SNK_OK, SNK_ERR_INVALID_ARG, SNK_ERR_CUDA, SNK_ERR_OOM, SNK_ERR_TIMEOUT, SNK_ERR_DEVICE_CHECK, SNK_ERR_OVERFLOW = range(7)
 SNK_CAM_AFFINE, SNK_CAM_RPC3 = 0, 1
 SNK_FP32, SNK_MIXED, SNK_MIXED_E4M3 = 0, 1, 2
+SNK_SAMPLE_SEGMENTS, SNK_SAMPLE_UNIFORM, SNK_SAMPLE_POINTS = 0, 1, 2
 STATUS_OVERFLOW, STATUS_CHECK, STATUS_TIMEOUT = 1, 2, 4
 
 
@@ -45,7 +46,7 @@ class SnkLayout(Structure):
 
 class SnkSampler(Structure):
     _fields_ = [("K_ray", c_int32), ("K_min", c_int32), ("K_max", c_int32), ("render", c_int32),
-                ("seed", c_uint32), ("iteration", c_uint32), ("occ_res", c_int32), ("reserved", c_int32),
+                ("seed", c_uint32), ("iteration", c_uint32), ("occ_res", c_int32), ("mode", c_int32),
                 ("occupancy", c_void_p)]
 
 
@@ -203,11 +204,12 @@ def model_struct(L, F, log2_T, n_min, n_max, geo_out, colour, shared_colour, n_s
     return SnkModel(L, F, log2_T, n_min, n_max, hidden, geo_out, int(colour), int(shared_colour), n_slots, precision)
 
 
-def sampler_struct(K_ray, K_min, K_max, render=0, seed=0, iteration=0, occupancy=None, occ_res=0):
+def sampler_struct(K_ray, K_min, K_max, render=0, seed=0, iteration=0, occupancy=None, occ_res=0, mode=0):
     """occupancy: device uint8 tensor [n_slots][occ_res^3] of occupied flags (culling), or None.
-    The struct keeps the tensor's address only: the caller keeps the tensor alive while it is used."""
+    The struct keeps the tensor's address only: the caller keeps the tensor alive while it is used.
+    mode: SNK_SAMPLE_SEGMENTS, SNK_SAMPLE_UNIFORM or SNK_SAMPLE_POINTS."""
     return SnkSampler(K_ray, K_min, K_max, render, seed & 0xFFFFFFFF, iteration & 0xFFFFFFFF,
-                      occ_res if occupancy is not None else 0, 0, ptr(occupancy))
+                      occ_res if occupancy is not None else 0, mode, ptr(occupancy))
 
 
 def adam_struct(lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, l2_mlp=1e-6):

@@ -97,3 +97,28 @@ def gpu_to_ray_major(seg_n, seg_off, ray_off_oracle):
                 idx[p:p + n] = int(seg_off[r, s]) + np.arange(n)
                 p += n
     return idx
+
+
+def gpu_sample(ctx, case, sp, cap=None):
+    """snk_sample_segments of the case's pixels with sampler sp; host copies of every output."""
+    import ctypes
+    import torch
+    from paper_2507_01631_b300 import snk
+    w = case.w
+    B = len(case.pix)
+    nseg = 1 + (w.nx == 2) + (w.ny == 2)
+    if cap is None:
+        cap = B * max(nseg * w.K_max, w.K_ray) + 512
+    f32, i32, u8 = torch.float32, torch.int32, torch.uint8
+    g = {k: torch.zeros(n, dtype=t, device="cuda") for k, n, t in
+         [("ray_od", 6 * B, f32), ("ray_ok", B, u8), ("seg_slot", 3 * B, u8), ("seg_t", 6 * B, f32),
+          ("seg_n", 3 * B, i32), ("seg_off", 3 * B, i32), ("smp_t", cap, f32), ("smp_dt", cap, f32),
+          ("smp_xyz", 3 * cap, f32), ("state", snk.STATE_WORDS, i32)]}
+    pix = torch.from_numpy(np.ascontiguousarray(case.pix.view(np.int32))).cuda()
+    ctx.call("snk_sample_segments", ctypes.byref(snk.window_struct(w.window())), snk.ptr(pix), B, ctypes.byref(sp),
+             *[snk.ptr(g[k]) for k in ("ray_od", "ray_ok", "seg_slot", "seg_t", "seg_n", "seg_off", "smp_t",
+                                       "smp_dt", "smp_xyz")], cap, snk.ptr(g["state"]), None)
+    torch.cuda.synchronize()
+    h = {k: v.cpu().numpy() for k, v in g.items()}
+    h["n_samples"] = int(h["state"][3:4].view(np.uint32)[0])
+    return h
