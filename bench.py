@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage-timing", type=int, default=1)
     ap.add_argument("--autotune", type=int, default=1, help="pick the launch shapes on the first batch first")
+    ap.add_argument("--red-ceiling", type=int, default=1,
+                    help="also time a stand-alone scatter of the step's table-gradient reductions")
     return ap.parse_args()
 
 
@@ -288,6 +290,49 @@ def time_graph(torch, tr, batches, steps):
     return e0.elapsed_time(e1), int(sum(int(c.item()) & 0xFFFFFFFF for c in counts))
 
 
+def reduction_ceiling(torch, snk, ctx, w, pix, sampler, params, field_backward_ms):
+    """Time the library's stand-alone scatter (snk_encode_backward: one thread per sample and
+    level, full occupancy, nothing else running) on the samples of one batch: the rate at which
+    this GPU retires the step's table-gradient reductions (8 float2 per sample and level).  The
+    fused backward does the same reductions while it runs the MLP backward."""
+    import ctypes
+    from paper_2507_01631_b300.autograd import Stages
+    from paper_2507_01631_b300.trainer import model_from_workload
+    m32 = model_from_workload(w, snk.SNK_FP32)
+    st = Stages(ctx, m32, snk.window_struct(w.window()))
+    batch = st.sample(pix, sampler)
+    torch.cuda.synchronize()
+    extent = int(batch.state[11].item()) & 0xFFFFFFFF    # slot_base[4]: end of the slot-major samples
+    n_samples = int(batch.state[3].item()) & 0xFFFFFFFF
+    p = torch.from_numpy(np.asarray(params, np.float32)).cuda()
+    grads = torch.zeros_like(p)
+    dfeat = torch.randn(extent, w.L * w.F, device="cuda")
+    ps = snk.SnkParams(snk.ptr(p), None, snk.ptr(grads), None, None, None)
+
+    def run():
+        ctx.call("snk_encode_backward", ctypes.byref(m32), ctypes.byref(ps), snk.ptr(batch.smp_xyz),
+                 snk.ptr(batch.state), extent, snk.ptr(dfeat), None)
+    run()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    reds = n_samples * w.L * 8
+    out = {"standalone_scatter_ms": ms, "reductions_per_step": reds, "standalone_reductions_per_s": reds / ms * 1e3,
+           "samples": n_samples}
+    if field_backward_ms:
+        out.update({"field_backward_ms": field_backward_ms, "fused_reductions_per_s": reds / field_backward_ms * 1e3,
+                    "fused_over_standalone": ms / field_backward_ms})
+    del dfeat, grads, batch
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -385,6 +430,10 @@ def run_ours(args, w):
         gms, gs = time_graph(torch, tr, batches, args.steps)
         extra["graph_replay"] = {"value": gs / (gms / 1000.0), "unit": "samples/s", "ms_per_step": gms / args.steps,
                                  "steps": args.steps}
+    if args.red_ceiling and args.precision == "mixed":
+        fb = stages.get("field_backward")
+        extra["l2_reduction_ceiling"] = reduction_ceiling(torch, snk, ctx, w, batches[0], sampler, params,
+                                                          fb[0] / max(fb[1], 1) if fb else None)
     if args.compare_fp32 and args.precision == "mixed":
         m32 = model_from_workload(w, snk.SNK_FP32)
         tr32 = Trainer(ctx, m32, snk.window_struct(w.window()), sampler, params)
