@@ -47,6 +47,8 @@ def parse():
                     help="also time the binary32 per-tile path on the same workload (mixed runs only)")
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--rays", type=int, default=0, help="override the workload's rays per step (profiling)")
+    ap.add_argument("--view-dirs", type=int, default=0,
+                    help="variant: colour input [g | SH_16(ray direction)] instead of g")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rays", type=int, default=256, help="rays per oracle sample (CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -173,7 +175,8 @@ def oracle_sample(w, cams, targets, params, seed, n_rays):
     from oracle import step as OS
     cfg = OS.ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, hidden=64,
                          geo_out=w.geo_out, colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots,
-                         K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max, first_layer=w.first_layer)
+                         K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max, first_layer=w.first_layer,
+                         view_dirs=w.view_dirs)
     pix = W.batch(w, cams, 1000 + seed, n_rays=n_rays)
     flat = params.astype(np.float64)
     n = len(flat)
@@ -199,7 +202,7 @@ def make_inputs(w, n_grid_params):
     cams = W.cameras(w)
     targets = synth.smooth_images(w.seed + 17, w.n_views, w.px, w.px)
     geo = [(64, w.L * w.F), (64, 64), (w.geo_out, 64)]
-    col = [(64, w.geo_out), (64, 64), (3, 64)] if w.colour else []
+    col = [(64, w.geo_out + (16 if w.view_dirs else 0)), (64, 64), (3, 64)] if w.colour else []
     n_col = (1 if w.shared_colour else w.n_slots) if w.colour else 0
     params = W.init_params(n_grid_params, geo, col, w.n_slots, n_col, w.seed)
     return cams, targets, params
@@ -527,6 +530,7 @@ def run_ours(args, w):
                    "views": "%d x %dpx %s" % (w.n_views, w.px, "rpc3" if w.cam_kind else "affine"),
                    "parallelism": "replicas" if world > 1 else "single",
                    "launch_shapes": tuning,
+                   **({"view_dirs": "SH degrees 0..3 of the ray direction"} if w.view_dirs else {}),
                    "l2": "working set per step > L2 (sample buffers %.2f GB)" % (n_samples / args.steps * 52 / 1e9)},
         "rays_per_s": st["n_accepted"] * args.steps / (ms / 1000.0) * world,
         "final_loss": st["loss"], "status": rc,
@@ -545,7 +549,12 @@ def run_ours(args, w):
 
 def main():
     args = parse()
-    w = W.get(args.workload, n_rays=args.rays) if args.rays > 0 else W.get(args.workload)
+    over = {}
+    if args.rays > 0:
+        over["n_rays"] = args.rays
+    if args.view_dirs:
+        over["view_dirs"] = True
+    w = W.get(args.workload, **over)
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -123,6 +123,11 @@ typedef struct {
     int32_t shared_colour;
     int32_t n_slots;
     int32_t precision; /* SNK_FP32, SNK_MIXED or SNK_MIXED_E4M3 */
+    int32_t view_dirs; /* 1: the colour MLP's input is [embedding | 16 real spherical harmonics of
+                        * degrees 0..3 of the ray's unit direction] (the view-direction variant,
+                        * after Instant-NGP's direction encoding); V1 is then [64][geo_out + 16].
+                        * Needs a colour MLP; used by snk_train_step and snk_render (the stage
+                        * calls have no ray directions and reject it) */
 } snk_model;
 
 /* Layout facts computed from a model on the host (no GPU needed). */

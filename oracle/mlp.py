@@ -11,6 +11,7 @@ NeRF-XL).  The paper gives no sizes; the workloads fix them:
   (the truncated exponential of Mueller et al. 2022);
 * colour MLP: G -> 64 -> 64 -> 3 on the whole embedding g, ReLU hidden,
   sigmoid output (no view direction: the synthetic scenes are Lambertian);
+  the view-direction variant feeds [g | SH_16(d)] (viewdir.py), G + 16 inputs;
 * without a colour net (G = 4) rgb = sigmoid(g_1..3).
 
 Weights are row-major W[out][in]; a layer computes y = W x.
@@ -26,8 +27,9 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
-def forward(feat, geo, col):
-    """feat (S, in) float64; geo = [W1, W2, W3]; col = [V1, V2, V3] or None.
+def forward(feat, geo, col, sh=None):
+    """feat (S, in) float64; geo = [W1, W2, W3]; col = [V1, V2, V3] or None;
+    sh (S, 16) view-direction encoding appended to the colour input, or None.
     Returns sigma (S,), rgb (S, 3) and the activations needed by backward."""
     acts = {"x0": feat}
     h = feat
@@ -45,7 +47,8 @@ def forward(feat, geo, col):
         rgb = sigmoid(g[:, 1:4])
         acts["col_pre"] = None
     else:
-        h = g
+        h = g if sh is None else np.concatenate([g, sh], 1)
+        acts["col_in"] = h
         cpre = []
         for li, V in enumerate(col):
             z = h @ V.T
@@ -71,7 +74,7 @@ def backward(dsigma, drgb, geo, col, acts):
         dg[:, 1:4] += dz_out
     else:
         cpre = acts["col_pre"]
-        ins = [g] + [relu(z) for z in cpre[:-1]]
+        ins = [acts.get("col_in", g)] + [relu(z) for z in cpre[:-1]]
         dcol = [None] * len(col)
         dz = dz_out
         for li in range(len(col) - 1, -1, -1):
@@ -80,7 +83,7 @@ def backward(dsigma, drgb, geo, col, acts):
             if li > 0:
                 dz = dh * (cpre[li - 1] > 0)
             else:
-                dg += dh
+                dg += dh[:, :g.shape[1]]  # the direction part of the input has no parameters behind it
     pre = acts["geo_pre"]
     ins = [acts["x0"]] + [relu(z) for z in pre[:-1]]
     dgeo = [None] * len(geo)

@@ -51,7 +51,8 @@ def update(cfg, flat, density, R, decay, threshold, seed, step):
         p = points(k, R, seed, step)
         smp = sampler.Samples(np.zeros(len(p), np.int64), np.full(len(p), k, np.int64), np.zeros(len(p), F32),
                               np.zeros(len(p), F32), p)
-        sigma, _, _ = field_forward(cfg, flat, smp)
+        # sigma does not depend on a view direction; any direction serves the colour input
+        sigma, _, _ = field_forward(cfg, flat, smp, dirs=np.array([[0.0, 0.0, -1.0]]))
         new[k] = np.maximum(decay * new[k], sigma)
         occ[k] = new[k] > min(threshold, new[k].mean())
     return new, occ

@@ -17,7 +17,7 @@ Flat parameter layout (also the library's):
 from dataclasses import dataclass, field
 import numpy as np
 
-from . import adam, camera, hashgrid, mlp, occupancy, quant, render, sampler
+from . import adam, camera, hashgrid, mlp, occupancy, quant, render, sampler, viewdir
 
 
 @dataclass
@@ -36,6 +36,7 @@ class ModelConfig:
     K_min: int = 64
     K_max: int = 64
     first_layer: str = "f16"    # "e4m3": the density MLP's input is quantised (quant.py)
+    view_dirs: bool = False     # colour input [g | SH_16(ray direction)] (viewdir.py)
 
     def grid(self):
         return hashgrid.layout(self.L, self.F, self.log2_T, self.n_min, self.n_max)
@@ -44,7 +45,8 @@ class ModelConfig:
         return [(self.hidden, self.L * self.F), (self.hidden, self.hidden), (self.geo_out, self.hidden)]
 
     def col_shapes(self):
-        return [(self.hidden, self.geo_out), (self.hidden, self.hidden), (3, self.hidden)] if self.colour else []
+        cin = self.geo_out + (16 if self.view_dirs else 0)
+        return [(self.hidden, cin), (self.hidden, self.hidden), (3, self.hidden)] if self.colour else []
 
     def tile_params(self):
         return self.grid().n_params + sum(a * b for a, b in self.geo_shapes())
@@ -141,8 +143,9 @@ def sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids=No
     return o, d, seg, smp
 
 
-def field_forward(cfg, flat, smp):
-    """sigma (S,), rgb (S, 3) and per-slot activations."""
+def field_forward(cfg, flat, smp, dirs=None):
+    """sigma (S,), rgb (S, 3) and per-slot activations.  dirs (B, 3): the rays'
+    unit directions (binary32), needed by the view-direction colour input."""
     lay = cfg.grid()
     tiles, cols = unflatten(cfg, flat)
     S = len(smp.t)
@@ -166,7 +169,8 @@ def field_forward(cfg, flat, smp):
         col = None
         if cfg.colour:
             col = cols[0] if cfg.shared_colour else cols[s]
-        sg, rg, acts = mlp.forward(feat, geo, col)
+        sh = viewdir.sh16(dirs[smp.ray[m]].astype(np.float64)) if (cfg.view_dirs and col is not None) else None
+        sg, rg, acts = mlp.forward(feat, geo, col, sh)
         sigma[m] = sg
         rgb[m] = rg
         acts["scale"] = scale
@@ -181,7 +185,7 @@ def train_step(cfg, flat, m_state, v_state, steps, cameras, win, pix, targets, s
     returned in extra["steps"]).  lr: Adam learning rate (I-NGP's 1e-2 unless given).
     occ: (occupied flags, R) of the slots' occupancy grids to cull samples, or None."""
     o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, False, occ=occ, mode=mode)
-    sigma, rgb_s, saved = field_forward(cfg, flat, smp)
+    sigma, rgb_s, saved = field_forward(cfg, flat, smp, dirs=d)
     rgb, depth, opac, tfin, _ = render.composite(sigma, rgb_s, smp.t.astype(np.float64),
                                                  smp.dt.astype(np.float64), seg.ray_off)
     gt = gather_targets(cameras, pix, targets)
@@ -224,7 +228,7 @@ def render_rays(cfg, flat, cameras, win, pix, seed=0, iteration=0, render_mode=T
     """Forward only: per-ray rgb, depth, opacity (bin-centre samples unless
     render_mode is False, then the training jitter of the given ray ids)."""
     o, d, seg, smp = sample_rays(cfg, cameras, win, pix, seed, iteration, render_mode, ray_ids, occ=occ, mode=mode)
-    sigma, rgb_s, _ = field_forward(cfg, flat, smp)
+    sigma, rgb_s, _ = field_forward(cfg, flat, smp, dirs=d)
     rgb, depth, opac, tfin, _ = render.composite(sigma, rgb_s, smp.t.astype(np.float64),
                                                  smp.dt.astype(np.float64), seg.ray_off)
     res = StepResult(seg, smp, sigma, rgb_s, rgb, depth, opac, tfin)

@@ -113,6 +113,9 @@ int layout_of(const snk_model *m, snk_layout *o, char *msg, size_t msg_len) {
   if (m->n_slots < 1 || m->n_slots > kMaxSlots) return bad("n_slots must be in 1..4");
   if (m->precision != SNK_FP32 && m->precision != SNK_MIXED && m->precision != SNK_MIXED_E4M3)
     return bad("precision must be SNK_FP32, SNK_MIXED or SNK_MIXED_E4M3");
+  if (m->view_dirs != 0 && m->view_dirs != 1) return bad("view_dirs must be 0 or 1");
+  if (m->view_dirs && !m->colour) return bad("view_dirs needs a colour MLP");
+  if (m->view_dirs && m->precision == SNK_MIXED_E4M3) return bad("view_dirs is not available with SNK_MIXED_E4M3");
   memset(o, 0, sizeof(*o));
   const int64_t T = (int64_t)1 << m->log2_T;
   const double b = m->L > 1 ? std::exp((std::log((double)m->n_max) - std::log((double)m->n_min)) / (m->L - 1)) : 1.0;
@@ -133,7 +136,8 @@ int layout_of(const snk_model *m, snk_layout *o, char *msg, size_t msg_len) {
   o->grid_params = off * m->F;
   const int64_t geo = (int64_t)kHidden * in + (int64_t)kHidden * kHidden + (int64_t)m->geo_out * kHidden;
   o->tile_params = o->grid_params + geo;
-  o->colour_params = m->colour ? (int64_t)kHidden * m->geo_out + (int64_t)kHidden * kHidden + 3 * kHidden : 0;
+  const int64_t col_in = m->geo_out + (m->view_dirs ? 16 : 0);
+  o->colour_params = m->colour ? (int64_t)kHidden * col_in + (int64_t)kHidden * kHidden + 3 * kHidden : 0;
   o->n_colour_blocks = m->colour ? (m->shared_colour ? 1 : m->n_slots) : 0;
   o->n_params = m->n_slots * o->tile_params + o->n_colour_blocks * o->colour_params;
   o->n_optimisers = m->n_slots + o->n_colour_blocks;
@@ -158,6 +162,8 @@ ModelDev model_dev(const snk_model *m, const snk_layout &lay) {
   d.n_slots = m->n_slots;
   d.mixed = m->precision != SNK_FP32;
   d.e4m3 = m->precision == SNK_MIXED_E4M3;
+  d.view_dirs = m->view_dirs;
+  d.col_in = m->geo_out + (m->view_dirs ? 16 : 0);
   d.tile_params = lay.tile_params;
   d.grid_params = lay.grid_params;
   d.colour_params = lay.colour_params;
@@ -166,7 +172,7 @@ ModelDev model_dev(const snk_model *m, const snk_layout &lay) {
   d.w2 = d.w1 + (int64_t)kHidden * d.in_dim;
   d.w3 = d.w2 + (int64_t)kHidden * kHidden;
   d.v1 = 0;
-  d.v2 = (int64_t)kHidden * m->geo_out;
+  d.v2 = (int64_t)kHidden * d.col_in;
   d.v3 = d.v2 + (int64_t)kHidden * kHidden;
   return d;
 }
@@ -257,6 +263,7 @@ size_t layout_ws(snk_ctx *ctx, char *base, int64_t B, int64_t S) {
   rb.smp_t = (float *)(base + carve(off, sizeof(float) * S));
   rb.smp_dt = (float *)(base + carve(off, sizeof(float) * S));
   rb.smp_xyz = (float *)(base + carve(off, sizeof(float) * 3 * S));
+  rb.smp_ray = (uint32_t *)(base + carve(off, sizeof(uint32_t) * S));
   float *sr = (float *)(base + carve(off, sizeof(float) * 4 * S));
   float *dsr = (float *)(base + carve(off, sizeof(float) * 4 * S));
   uint16_t *flp = (uint16_t *)(base + carve(off, sizeof(uint16_t) * 64 * (S + 128)));
@@ -451,6 +458,7 @@ int snk_sample_segments(snk_ctx *ctx, const snk_window *win, const uint32_t *pix
   rb.smp_t = smp_t;
   rb.smp_dt = smp_dt;
   rb.smp_xyz = smp_xyz;
+  rb.smp_ray = nullptr;  // caller-sized buffers: the workspace's per-sample ray index may be shorter than cap
   SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, rb, cap, state,
                                      (cudaStream_t)stream, ctx->tune));
   return SNK_OK;
@@ -506,6 +514,8 @@ int snk_mlp(snk_ctx *ctx, const snk_model *model, const snk_params *p, const flo
   if (rc) return rc;
   if (!p || !p->params || !feat || !state || !out || S < 0)
     return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative S");
+  if (model->view_dirs)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_mlp: the view-direction colour input needs the rays; use the step entry points");
   FieldArgs fa{};
   fa.m = md;
   fa.params = p->params;
@@ -527,6 +537,8 @@ int snk_mlp_backward(snk_ctx *ctx, const snk_model *model, const snk_params *p, 
   if (rc) return rc;
   if (!p || !p->params || !p->grads || !feat || !state || !dout || !dfeat || S < 0)
     return fail(ctx, SNK_ERR_INVALID_ARG, "NULL buffer or negative S");
+  if (model->view_dirs)
+    return fail(ctx, SNK_ERR_INVALID_ARG, "snk_mlp_backward: the view-direction colour input needs the rays; use the step entry points");
   FieldArgs fa{};
   fa.m = md;
   fa.params = p->params;
@@ -580,8 +592,18 @@ int snk_composite_backward(snk_ctx *ctx, const float *sigma_rgb, const float *sm
   return SNK_OK;
 }
 
+// The workspace's ray buffers for a step of `model`: the per-sample ray index is written only
+// when the colour input needs the view direction.
+static RayBuffers step_rays(const snk_ctx *ctx, const snk_model *model) {
+  RayBuffers rb = ctx->rb;
+  if (!model->view_dirs) rb.smp_ray = nullptr;
+  return rb;
+}
+
+// n_rays: the batch size of the rays whose directions ray_od holds ([6][n_rays]); every
+// sample's ray index (rb.smp_ray) is below it.
 static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, const snk_params *p,
-                     const snk_state *state, int mode, cudaStream_t st) {
+                     const snk_state *state, int mode, cudaStream_t st, int n_rays) {
   FieldArgs fa{};
   fa.m = md;
   fa.params = p->params;
@@ -597,6 +619,9 @@ static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, c
   fa.state = state;
   fa.S = ctx->cap_samples;
   fa.mode = mode;
+  fa.smp_ray = ctx->rb.smp_ray;
+  fa.ray_od = ctx->rb.ray_od;
+  fa.n_rays = n_rays;
   if (model->precision != SNK_FP32) {
     fa.slot_only = -1;
     if (md.e4m3 && mode == kForward) {
@@ -636,12 +661,12 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   const cudaStream_t st = (cudaStream_t)stream;
   {
     StageMark m(ctx, 0, st);
-    SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, ctx->rb, ctx->cap_samples, state,
+    SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, step_rays(ctx, model), ctx->cap_samples, state,
                                        st, ctx->tune));
   }
   {
     StageMark m(ctx, 1, st);
-    if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B))) return rc;
   }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
@@ -662,7 +687,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   }
   {
     StageMark m(ctx, 3, st);
-    if ((rc = run_field(ctx, model, md, p, state, kBackward, st))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kBackward, st, B))) return rc;
   }
   AdamArgs aa{};
   aa.params = p->params;
@@ -717,12 +742,12 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   const cudaStream_t st = (cudaStream_t)stream;
   {
     StageMark m(ctx, 0, st);
-    SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state,
+    SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, step_rays(ctx, model), ctx->cap_samples, state,
                                        st, ctx->tune));
   }
   {
     StageMark m(ctx, 1, st);
-    if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B))) return rc;
   }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
@@ -822,12 +847,12 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
     return ms / reps;
   };
   auto sample = [&]() -> int {
-    if (launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, ctx->rb, ctx->cap_samples, state, st,
+    if (launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 0, step_rays(ctx, model), ctx->cap_samples, state, st,
                                ctx->tune) != cudaSuccess)
       return fail(ctx, SNK_ERR_CUDA, "snk_autotune: sampling failed");
     return SNK_OK;
   };
-  auto field = [&](int mode) { return run_field(ctx, model, md, &ps, state, mode, st); };
+  auto field = [&](int mode) { return run_field(ctx, model, md, &ps, state, mode, st, B); };
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
   ca.smp_t = ctx->rb.smp_t;
@@ -998,12 +1023,13 @@ int snk_occupancy_update(snk_ctx *ctx, const snk_model *model, const snk_params 
     ctx->occ_ws_bytes = need;
   }
   snk_state *state = static_cast<snk_state *>(ctx->occ_ws);
+  // sigma, the only output used, does not depend on the view direction: every point takes ray 0
   float *partial = reinterpret_cast<float *>(static_cast<char *>(ctx->occ_ws) + 256);
   float *thr = partial + occ_partials(model->n_slots, R);
   const cudaStream_t st = (cudaStream_t)stream;
   SNK_CK(ctx, cudaMemsetAsync(state, 0, sizeof(snk_state), st));
-  SNK_CK(ctx, launch_occ_points(model->n_slots, R, seed, step, ctx->rb.smp_xyz, state, st));
-  if ((rc = run_field(ctx, model, md, p, state, kForward, st))) return rc;
+  SNK_CK(ctx, launch_occ_points(model->n_slots, R, seed, step, ctx->rb.smp_xyz, ctx->rb.smp_ray, state, st));
+  if ((rc = run_field(ctx, model, md, p, state, kForward, st, 1))) return rc;
   SNK_CK(ctx, launch_occ_update(model->n_slots, R, ctx->sigma_rgb, decay, threshold, density, occupancy, partial, thr,
                                 st));
   return SNK_OK;

@@ -112,6 +112,32 @@ __device__ __forceinline__ uint32_t occ_cell(const float l[3], int R) {
   return (c[2] * (uint32_t)R + c[1]) * (uint32_t)R + c[0];
 }
 
+// ---- view-direction encoding -------------------------------------------------
+// The 16 real spherical harmonics of degrees 0..3 of a unit direction (x, y, z), in the order
+// (l, m) = (0, 0), (1, -1), (1, 0), (1, 1), (2, -2), ..., (3, 3), with the sign convention of the
+// usual graphics tables (Instant-NGP's direction encoding); the constants are the normalisations
+// sqrt((2l + 1) / 4 pi (l - |m|)! / (l + |m|)!) (times sqrt 2 for m != 0) folded with the
+// polynomial coefficients.
+__device__ __forceinline__ void sh16(float x, float y, float z, float (&v)[16]) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  v[0] = 0.28209479177387814f;
+  v[1] = -0.48860251190291987f * y;
+  v[2] = 0.48860251190291987f * z;
+  v[3] = -0.48860251190291987f * x;
+  v[4] = 1.0925484305920792f * x * y;
+  v[5] = -1.0925484305920792f * y * z;
+  v[6] = 0.94617469575756008f * zz - 0.31539156525252005f;
+  v[7] = -1.0925484305920792f * x * z;
+  v[8] = 0.54627421529603959f * (xx - yy);
+  v[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+  v[10] = 2.8906114426405538f * x * y * z;
+  v[11] = 0.45704579946446572f * y * (1.0f - 5.0f * zz);
+  v[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);
+  v[13] = 0.45704579946446572f * x * (1.0f - 5.0f * zz);
+  v[14] = 1.4453057213202769f * z * (xx - yy);
+  v[15] = 0.59004358992664352f * x * (3.0f * yy - xx);
+}
+
 // ---- NGP dense index / spatial hash ----------------------------------------
 __device__ __forceinline__ uint32_t grid_index(uint32_t x, uint32_t y, uint32_t z, int N, bool dense, uint32_t Tmask) {
   if (dense) {

@@ -11,6 +11,11 @@
 // in shared memory.  Weight gradients live in registers (each thread owns a
 // fixed set of weights) for the whole persistent loop and are flushed with
 // one atomic per weight when the block moves to another slot and at exit.
+//
+// View-direction variant (VD): the colour MLP's input row is [g | SH_16(d)],
+// the 16 real spherical harmonics of the sample's ray direction written next
+// to g in the same shared-memory row; the input gradient of that layer is
+// taken over the g columns only.
 #include "kernels.cuh"
 
 namespace snk {
@@ -19,10 +24,11 @@ namespace {
 constexpr int NS = 64;   // samples per tile
 constexpr int NT = 128;  // threads per block
 
-template <int IN, int G, bool COL>
+template <int IN, int G, bool COL, bool VD>
 struct Dims {
   static constexpr int H = kHidden;
-  static constexpr int S0 = IN + 1, SH = H + 1, SG = G + 1;
+  static constexpr int CIN = G + (VD ? 16 : 0);  // colour input width
+  static constexpr int S0 = IN + 1, SH = H + 1, SG = CIN + 1;
   static constexpr int X0 = 0;
   static constexpr int X1 = X0 + NS * S0;
   static constexpr int X2 = X1 + NS * SH;
@@ -36,7 +42,7 @@ struct Dims {
   static constexpr int NW1 = H * IN / NT;
   static constexpr int NW2 = H * H / NT;
   static constexpr int NW3 = (G * H + NT - 1) / NT;
-  static constexpr int NV1 = COL ? (H * G + NT - 1) / NT : 1;
+  static constexpr int NV1 = COL ? (H * CIN + NT - 1) / NT : 1;
   static constexpr int NV2 = COL ? H * H / NT : 1;
   static constexpr int NV3 = COL ? (3 * H + NT - 1) / NT : 1;
 };
@@ -64,8 +70,9 @@ __device__ __forceinline__ void layer_fwd(const float *__restrict__ W, const flo
   }
 }
 
-// dx[s][i] = (mask ? act[s][i] > 0 : 1) * sum_o W[o][i] d[s][o] for i = hh, hh + 2, ...
-template <int I, int O, bool MASK>
+// dx[s][i] = (mask ? act[s][i] > 0 : 1) * sum_o W[o][i] d[s][o] for i = hh, hh + 2, ... < I
+// (W row-major with rows of LD >= I weights).
+template <int I, int O, bool MASK, int LD = I>
 __device__ __forceinline__ void layer_bwd(const float *__restrict__ W, const float *d_row, const float *act_row,
                                           float *dx_row, int hh) {
   float d[O];
@@ -74,7 +81,7 @@ __device__ __forceinline__ void layer_bwd(const float *__restrict__ W, const flo
   for (int i = hh; i < I; i += 2) {
     float acc = 0.0f;
 #pragma unroll
-    for (int o = 0; o < O; ++o) acc = fmaf(__ldg(W + (size_t)o * I + i), d[o], acc);
+    for (int o = 0; o < O; ++o) acc = fmaf(__ldg(W + (size_t)o * LD + i), d[o], acc);
     if (MASK) acc = act_row[i] > 0.0f ? acc : 0.0f;
     dx_row[i] = acc;
   }
@@ -106,9 +113,10 @@ __device__ __forceinline__ void flush_dw(float *acc, float *dst, int tid) {
   }
 }
 
-template <int IN, int G, bool COL, int MODE>
+template <int IN, int G, bool COL, bool VD, int MODE>
 __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
-  using D = Dims<IN, G, COL>;
+  using D = Dims<IN, G, COL, VD>;
+  constexpr int CIN = D::CIN;
   constexpr int H = kHidden;
   extern __shared__ float sm[];
   float *X0 = sm + D::X0, *X1 = sm + D::X1, *X2 = sm + D::X2, *X3 = sm + D::X3, *X4 = sm + D::X4,
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
     flush_dw<D::NW3, G * H>(aW3, g + m.w3, tid);
     if (COL) {
       float *c = a.grads + m.colour_base + (m.shared_colour ? 0 : (int64_t)k * m.colour_params);
-      flush_dw<D::NV1, H * G>(aV1, c + m.v1, tid);
+      flush_dw<D::NV1, H * CIN>(aV1, c + m.v1, tid);
       flush_dw<D::NV2, H * H>(aV2, c + m.v2, tid);
       flush_dw<D::NV3, 3 * H>(aV3, c + m.v3, tid);
     }
@@ -209,6 +217,18 @@ __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
         }
       }
     }
+    if (VD && MODE != kEncodeOnly && hh == 0) {
+      // colour input columns G .. G + 15: SH of the sample's ray direction
+      float d[3] = {0.f, 0.f, 1.f}, v[16];
+      if (valid) {
+        const uint32_t r = a.smp_ray[idx];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) d[q] = a.ray_od[(int64_t)(3 + q) * a.n_rays + r];
+      }
+      sh16(d[0], d[1], d[2], v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) X3[s * D::SG + G + j] = v[j];
+    }
     __syncthreads();
     if (MODE == kEncodeOnly) continue;
 
@@ -220,7 +240,7 @@ __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
     layer_fwd<H, G, false>(Wg3, X2 + s * D::SH, X3 + s * D::SG, hh);
     __syncthreads();
     if (COL) {
-      layer_fwd<G, H, true>(V1, X3 + s * D::SG, X4 + s * D::SH, hh);
+      layer_fwd<CIN, H, true>(V1, X3 + s * D::SG, X4 + s * D::SH, hh);
       __syncthreads();
       layer_fwd<H, H, true>(V2, X4 + s * D::SH, X5 + s * D::SH, hh);
       __syncthreads();
@@ -273,8 +293,8 @@ __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
       accum_dw<D::NV2, H, H>(aV2, DA, D::SH, X4, D::SH, tid);
       __syncthreads();
       // delta of g (into DA) = V1^T delta_c1 + (dsigma term on g0), dV1 = delta_c1 (x) g
-      layer_bwd<G, H, false>(V1, X5 + s * D::SH, nullptr, DA + s * D::SH, hh);
-      accum_dw<D::NV1, H, G>(aV1, X5, D::SH, X3, D::SG, tid);
+      layer_bwd<G, H, false, CIN>(V1, X5 + s * D::SH, nullptr, DA + s * D::SH, hh);
+      accum_dw<D::NV1, H, CIN>(aV1, X5, D::SH, X3, D::SG, tid);
       __syncthreads();
       if (hh == 0) DA[s * D::SH + 0] += OUT[s * 4 + 0];
       __syncthreads();
@@ -326,11 +346,11 @@ __global__ void __launch_bounds__(NT, 2) k_field_fp32(const FieldArgs a) {
   if (MODE == kBackward && cur_slot >= 0) flush(cur_slot);
 }
 
-template <int IN, int G, bool COL, int MODE>
+template <int IN, int G, bool COL, bool VD, int MODE>
 cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int ctas_per_sm) {
-  using D = Dims<IN, G, COL>;
+  using D = Dims<IN, G, COL, VD>;
   const size_t smem = sizeof(float) * D::TOTAL;
-  auto k = k_field_fp32<IN, G, COL, MODE>;
+  auto k = k_field_fp32<IN, G, COL, VD, MODE>;
   static bool attr_done = false;  // per instantiation; the attribute is per device function
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -346,19 +366,23 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int ctas
   return cudaGetLastError();
 }
 
-template <int IN, int G, bool COL>
+template <int IN, int G, bool COL, bool VD>
 cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, int c) {
   switch (a.mode) {
-    case kEncodeOnly: return launch_t<IN, G, COL, kEncodeOnly>(a, sm_count, st, c);
-    case kForward: return launch_t<IN, G, COL, kForward>(a, sm_count, st, c);
-    default: return launch_t<IN, G, COL, kBackward>(a, sm_count, st, c);
+    case kEncodeOnly: return launch_t<IN, G, COL, VD, kEncodeOnly>(a, sm_count, st, c);
+    case kForward: return launch_t<IN, G, COL, VD, kForward>(a, sm_count, st, c);
+    default: return launch_t<IN, G, COL, VD, kBackward>(a, sm_count, st, c);
   }
 }
 
 template <int IN>
 cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st, int c) {
-  if (a.m.colour) return launch_mode<IN, 16, true>(a, sm_count, st, c);
-  return launch_mode<IN, 4, false>(a, sm_count, st, c);
+  if (a.m.colour && a.m.view_dirs && a.mode != kEncodeOnly) {
+    if (a.smp_ray == nullptr || a.ray_od == nullptr || a.n_rays < 1) return cudaErrorInvalidValue;
+    return launch_mode<IN, 16, true, true>(a, sm_count, st, c);
+  }
+  if (a.m.colour) return launch_mode<IN, 16, true, false>(a, sm_count, st, c);
+  return launch_mode<IN, 4, false, false>(a, sm_count, st, c);
 }
 
 // Thread per (sample, level): trilinear scatter-add of a feature gradient.

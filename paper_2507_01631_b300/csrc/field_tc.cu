@@ -31,6 +31,13 @@
 // tensor core and frees the tensor memory before returning.  Decisions that
 // end the MMA warps' loop are made uniform over those warps (bar.red.or) and
 // also release the scatter warps' waits through a shared abort flag.
+//
+// View-direction variant (VD): the colour MLP's input is [g | SH_16(d)], a
+// [128 x 32] operand whose columns 16..31 hold the spherical harmonics of each
+// sample's ray direction (hi and lo parts like every other operand).  In the
+// core-matrix layout the first 16 columns of a 32-column buffer sit exactly
+// where a 16-column buffer would put them, so the input-gradient MMA of that
+// layer runs with N = 16 on the [64 x 32] weights and yields dg alone.
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -52,9 +59,10 @@ constexpr float kLoScale = 2048.0f, kLoInv = 1.0f / 2048.0f;
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <int IN, bool BWD>
+template <int IN, bool BWD, bool VD>
 struct L {
   static constexpr int INP = IN < 16 ? 16 : IN;  // layer-1 K padded to the MMA K step
+  static constexpr int CIN = VD ? 32 : 16;        // colour input width (K of the first colour layer)
   // backward deltas (high parts) first: the padded MN-major reads of dW run up
   // to 32 KB past a delta buffer and must stay inside the allocation
   static constexpr int DA = 0;                                 // [128 x 64]
@@ -73,14 +81,14 @@ struct L {
   static constexpr int X0 = LO_END;                            // [128 x INP]
   static constexpr int X1 = X0 + TM * INP * 2;                 // h1  [128 x 64]
   static constexpr int X2 = X1 + TM * 64 * 2;                  // h2
-  static constexpr int X3 = BWD ? X2 + TM * 64 * 2 : X2;       // g [128 x 16] (forward: h2's buffer)
-  static constexpr int X4 = BWD ? X3 + TM * 16 * 2 : X1;       // c1 (forward: h1's buffer)
+  static constexpr int X3 = BWD ? X2 + TM * 64 * 2 : X2;       // g [128 x CIN] (forward: h2's buffer)
+  static constexpr int X4 = BWD ? X3 + TM * CIN * 2 : X1;      // c1 (forward: h1's buffer)
   static constexpr int X5 = BWD ? X4 + TM * 64 * 2 : X2;       // c2 (forward: h2's buffer)
   static constexpr int W1 = BWD ? X5 + TM * 64 * 2 : X2 + TM * 64 * 2;  // [64 x INP]
   static constexpr int W2 = W1 + 64 * INP * 2;                 // [64 x 64]
   static constexpr int W3 = W2 + 64 * 64 * 2;                  // [16 x 64]
-  static constexpr int V1 = W3 + 16 * 64 * 2;                  // [64 x 16]
-  static constexpr int V2 = V1 + 64 * 16 * 2;                  // [64 x 64]
+  static constexpr int V1 = W3 + 16 * 64 * 2;                  // [64 x CIN]
+  static constexpr int V2 = V1 + 64 * CIN * 2;                 // [64 x 64]
   static constexpr int V3 = V2 + 64 * 64 * 2;                  // [16 x 64]
   static constexpr int END = V3 + 16 * 64 * 2;
   // backward: two [128 x (IN + 4)] binary32 feature-gradient buffers handed to the scatter warps
@@ -228,10 +236,11 @@ struct TileInfo {
   int32_t n_valid;  // rows 0 .. n_valid-1 are samples of the slot
 };
 
-template <int IN, int G, bool COL, bool BWD, bool Q8, int KL>
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD>
 __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
-  using Y = L<IN, BWD>;
+  using Y = L<IN, BWD, VD>;
   constexpr int INP = Y::INP;
+  constexpr int CIN = Y::CIN;
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + Y::MISC);
   uint64_t *full = mbar + 1;   // [2] the MMA warps filled DF[b] (TT arrivals)
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
       float *dst;
     };
     const R regs[6] = {{Y::C_W1, INP, 64, IN, gs + m.w1}, {Y::C_W2, 64, 64, 64, gs + m.w2},
-                       {Y::C_W3, 64, G, 64, gs + m.w3},   {Y::C_V1, 16, 64, G, gc + m.v1},
+                       {Y::C_W3, 64, G, 64, gs + m.w3},   {Y::C_V1, CIN, 64, VD ? CIN : G, gc + m.v1},
                        {Y::C_V2, 64, 64, 64, gc + m.v2},  {Y::C_V3, 64, 3, 64, gc + m.v3}};
     const int nreg = COL ? 6 : 3;
     // E4M3 first layer: the dW1 MMAs read the codes' values; the layer's input is scale x value
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
       load_weights(sm + Y::W2, P + m.w2, 64, 64, 64, 64);
       load_weights(sm + Y::W3, P + m.w3, G, 64, 16, 64);
       if (COL) {
-        load_weights(sm + Y::V1, C + m.v1, 64, G, 64, 16);
+        load_weights(sm + Y::V1, C + m.v1, 64, VD ? CIN : G, 64, CIN);
         load_weights(sm + Y::V2, C + m.v2, 64, 64, 64, 64);
         load_weights(sm + Y::V3, C + m.v3, 3, 64, 16, 64);
       }
@@ -563,12 +572,22 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
 #pragma unroll
         for (int k = 0; k < 3; ++k) rgb[k] = sigm(g[1 + k]);
       }
+    } else if (VD) {
+      // colour input columns 16..31: SH of the sample's ray direction
+      float dir[3] = {0.f, 0.f, 1.f}, y[16];
+      if (valid) {
+        const uint32_t ray = a.smp_ray[idx];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) dir[q] = a.ray_od[(int64_t)(3 + q) * a.n_rays + ray];
+      }
+      sh16(dir[0], dir[1], dir[2], y);
+      store16(sm + Y::X3 + TM * 16 * 2, sm + Y::XL3 + TM * 16 * 2, r, y);
     }
     handoff();
     if (COL) {
       if (t == 0) {
-        mma_fwd(tmem, s0 + Y::X3, s0 + Y::V1, 16, 64);
-        mma_fwd(tmem + Y::C_DL, s0 + Y::XL3, s0 + Y::V1, 16, 64);
+        mma_fwd(tmem, s0 + Y::X3, s0 + Y::V1, CIN, 64);
+        mma_fwd(tmem + Y::C_DL, s0 + Y::XL3, s0 + Y::V1, CIN, 64);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -655,11 +674,11 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
       if (abort) break;
       epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X4, r, ch);
       handoff();
-      // dg = delta_c1 * V1 (+ dsigma term), dV1 += delta_c1^T g
+      // dg = delta_c1 * V1 (+ dsigma term; N = 16: the g columns of V1), dV1 += delta_c1^T [g | SH]
       if (t == 0) {
         mma_dx(tmem, s0 + Y::DB, s0 + Y::V1, 64, 16);
         mma_dx(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::V1, 64, 16);
-        mma_dw(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, 16, acc);
+        mma_dw(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, CIN, acc);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -756,10 +775,13 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
   if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
 }
 
-template <int IN, int G, bool COL, bool BWD, bool Q8, int KL>
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD>
 cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_ctas) {
-  using Y = L<IN, BWD>;
-  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL>;
+  using Y = L<IN, BWD, VD>;
+  static_assert(Y::SMEM <= 232448, "shared memory per CTA");
+  static_assert(BWD || 2 * (Y::SMEM + 1024) <= 233472, "two forward CTAs per SM");
+  static_assert(Y::C_V1 + Y::CIN <= Y::C_DL || !BWD, "tensor-memory columns of dV1");
+  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL, VD>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
@@ -776,18 +798,22 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_
   return cudaGetLastError();
 }
 
-template <int IN, int G, bool COL, bool Q8>
+template <int IN, int G, bool COL, bool Q8, bool VD>
 cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
-  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8, 1>(a, sm_count, st, 1);
+  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8, 1, VD>(a, sm_count, st, 1);
   // the E4M3 forward reads its features instead of gathering them: no gather shape to pick
-  if (!Q8 && tu.tc_fwd_levels == 2) return launch_t<IN, G, COL, false, Q8, 2>(a, sm_count, st, tu.tc_fwd_ctas);
-  return launch_t<IN, G, COL, false, Q8, 1>(a, sm_count, st, tu.tc_fwd_ctas);
+  if (!Q8 && tu.tc_fwd_levels == 2) return launch_t<IN, G, COL, false, Q8, 2, VD>(a, sm_count, st, tu.tc_fwd_ctas);
+  return launch_t<IN, G, COL, false, Q8, 1, VD>(a, sm_count, st, tu.tc_fwd_ctas);
 }
 
 template <int IN, int G, bool COL>
 cudaError_t launch_q(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
-  if (a.m.e4m3) return launch_mode<IN, G, COL, true>(a, sm_count, st, tu);
-  return launch_mode<IN, G, COL, false>(a, sm_count, st, tu);
+  if (COL && a.m.view_dirs) {
+    if (a.m.e4m3 || a.smp_ray == nullptr || a.ray_od == nullptr || a.n_rays < 1) return cudaErrorInvalidValue;
+    return launch_mode<IN, G, COL, false, true>(a, sm_count, st, tu);
+  }
+  if (a.m.e4m3) return launch_mode<IN, G, COL, true, false>(a, sm_count, st, tu);
+  return launch_mode<IN, G, COL, false, false>(a, sm_count, st, tu);
 }
 
 template <int IN>

@@ -31,6 +31,7 @@ struct RayBuffers {
   float *smp_t;        // [cap]
   float *smp_dt;       // [cap]
   float *smp_xyz;      // [cap][3]
+  uint32_t *smp_ray;   // [cap] ray of each sample (the view-direction colour input), or null
 };
 
 int scan_blocks(int B);
@@ -43,6 +44,7 @@ struct ModelDev {
   GridParams grid;
   int32_t in_dim, geo_out, colour, shared_colour, n_slots, mixed;
   int32_t e4m3;  // mixed path with an E4M3 first-layer input (one scale per slot and step)
+  int32_t view_dirs, col_in;  // colour input [g | SH_16(direction)] and its width (geo_out + 16 view_dirs)
   int64_t tile_params, grid_params, colour_params, colour_base;
   int64_t w1, w2, w3;  // offsets of the density-MLP matrices inside a slot block
   int64_t v1, v2, v3;  // offsets of the colour-MLP matrices inside a colour block
@@ -66,6 +68,9 @@ struct FieldArgs {
   float *feat32;              // E4M3 path: [S][IN] binary32 features (gather writes, forward reads)
   uint8_t *codes;             // E4M3 path: [S][IN] first-layer codes (forward writes, backward reads)
   uint32_t *amax;             // E4M3 path: per slot, bits of max |feature| of the step (>= 0 floats)
+  const uint32_t *smp_ray;    // view-direction models: [S] ray of each sample
+  const float *ray_od;        // view-direction models: [6][n_rays] ray origins and directions
+  int32_t n_rays;
   const snk_state *state;
   int64_t S;                  // extent of the slot-major arrays
   int32_t slot_only;          // -1: every slot; k: only slot k (per-tile launches)
@@ -93,8 +98,8 @@ cudaError_t launch_ray_pool(const DevView *views, int n_views, const WinParams &
 cudaError_t launch_draw(const uint32_t *pool, const uint32_t *n_pool, int B, uint32_t seed, uint32_t iteration,
                         uint32_t *pix, cudaStream_t st);
 // Occupancy grid update (occupancy.cu).
-cudaError_t launch_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, float *xyz, snk_state *state,
-                              cudaStream_t st);
+cudaError_t launch_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, float *xyz, uint32_t *ray,
+                              snk_state *state, cudaStream_t st);
 int64_t occ_partials(int n_slots, int R);
 cudaError_t launch_occ_update(int n_slots, int R, const float *sigma_rgb, float decay, float threshold,
                               float *density, uint8_t *occ, float *partial, float *thr, cudaStream_t st);

@@ -19,7 +19,7 @@ namespace {
 constexpr int kOccThreads = 256;
 
 __global__ void k_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, float *__restrict__ xyz,
-                             snk_state *__restrict__ state) {
+                             uint32_t *__restrict__ ray, snk_state *__restrict__ state) {
   const int64_t R3 = (int64_t)R * R * R;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -35,6 +35,7 @@ __global__ void k_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, f
   const float inv = fdiv(1.0f, (float)R);
 #pragma unroll
   for (int a = 0; a < 3; ++a) xyz[i * 3 + a] = fmul(fadd((float)c[a], u32_to_unit(u[a])), inv);
+  ray[i] = 0u;
 }
 
 // density <- max(decay density, sigma); per-block partial sums of the new densities
@@ -79,10 +80,10 @@ __global__ void k_occ_binarize(int64_t n, int64_t R3, const float *__restrict__ 
 
 }  // namespace
 
-cudaError_t launch_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, float *xyz, snk_state *state,
-                              cudaStream_t st) {
+cudaError_t launch_occ_points(int n_slots, int R, uint32_t seed, uint32_t step, float *xyz, uint32_t *ray,
+                              snk_state *state, cudaStream_t st) {
   const int64_t n = (int64_t)n_slots * R * R * R;
-  k_occ_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n_slots, R, seed, step, xyz, state);
+  k_occ_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n_slots, R, seed, step, xyz, ray, state);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_o
                           const uint32_t *__restrict__ excl, const uint32_t *__restrict__ block_tot, int nb, int B,
                           WinParams win, SamplerParams smp, const snk_state *__restrict__ state,
                           const uint32_t *__restrict__ seg_k, uint32_t *__restrict__ seg_off,
-                          float *__restrict__ smp_t, float *__restrict__ smp_dt, float *__restrict__ smp_xyz) {
+                          float *__restrict__ smp_t, float *__restrict__ smp_dt, float *__restrict__ smp_xyz,
+                          uint32_t *__restrict__ smp_ray) {
   const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= B) return;
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(512) k_samples(const float *__restrict__ ray_o
         smp_dt[q] = dt;
 #pragma unroll
         for (int a = 0; a < 3; ++a) smp_xyz[q * 3 + a] = l[a];
+        if (smp_ray) smp_ray[q] = (uint32_t)r;
       }
       written += __popc(m);
     }
@@ -420,7 +422,8 @@ cudaError_t launch_sample_segments(const DevView *views, int n_views, const WinP
   const int64_t threads = (int64_t)B * 32;
   k_samples<<<(unsigned)((threads + nt - 1) / nt), nt, 0, st>>>(rb.ray_od, rb.seg_slot, rb.seg_t, rb.seg_n, rb.excl,
                                                                 rb.block_tot, nb, B, win, smp, state, rb.seg_k,
-                                                                rb.seg_off, rb.smp_t, rb.smp_dt, rb.smp_xyz);
+                                                                rb.seg_off, rb.smp_t, rb.smp_dt, rb.smp_xyz,
+                                                                rb.smp_ray);
   count_launches(4);
   return cudaGetLastError();
 }

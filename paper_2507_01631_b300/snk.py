@@ -34,7 +34,7 @@ class SnkWindow(Structure):
 
 class SnkModel(Structure):
     _fields_ = [(n, c_int32) for n in ("L", "F", "log2_T", "n_min", "n_max", "hidden", "geo_out", "colour",
-                                        "shared_colour", "n_slots", "precision")]
+                                        "shared_colour", "n_slots", "precision", "view_dirs")]
 
 
 class SnkLayout(Structure):
@@ -200,8 +200,10 @@ def window_struct(win):
     return w
 
 
-def model_struct(L, F, log2_T, n_min, n_max, geo_out, colour, shared_colour, n_slots, precision, hidden=64):
-    return SnkModel(L, F, log2_T, n_min, n_max, hidden, geo_out, int(colour), int(shared_colour), n_slots, precision)
+def model_struct(L, F, log2_T, n_min, n_max, geo_out, colour, shared_colour, n_slots, precision, hidden=64,
+                 view_dirs=False):
+    return SnkModel(L, F, log2_T, n_min, n_max, hidden, geo_out, int(colour), int(shared_colour), n_slots, precision,
+                    int(view_dirs))
 
 
 def sampler_struct(K_ray, K_min, K_max, render=0, seed=0, iteration=0, occupancy=None, occ_res=0, mode=0):

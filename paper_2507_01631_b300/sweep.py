@@ -236,7 +236,7 @@ def _main():
         model = model_from_workload(w)
         lay = snk.layout(model)
         geo = [(64, w.L * w.F), (64, 64), (w.geo_out, 64)]
-        col = [(64, w.geo_out), (64, 64), (3, 64)]
+        col = [(64, w.geo_out + (16 if w.view_dirs else 0)), (64, 64), (3, 64)]
         p0 = W.init_params(lay.grid_params, geo, col, 1, 1, w.seed)
         tile0, colour0 = p0[:lay.tile_params], p0[lay.tile_params:]
         sw = SnakeSweep(ctx, w, lambda t: tile0, colour0)

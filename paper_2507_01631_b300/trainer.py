@@ -19,7 +19,7 @@ def model_from_workload(w, precision=None, hidden=64):
             precision = snk.SNK_MIXED_E4M3 if getattr(w, "first_layer", "f16") == "e4m3" else snk.SNK_MIXED
     prec = precision
     return snk.model_struct(w.L, w.F, w.log2_T, w.n_min, w.n_max, w.geo_out, w.colour, w.shared_colour,
-                            w.n_slots, prec, hidden)
+                            w.n_slots, prec, hidden, view_dirs=getattr(w, "view_dirs", False))
 
 
 def low_precision_copy(params, lay, model):

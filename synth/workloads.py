@@ -44,6 +44,7 @@ class Workload:
     raster: int = 512
     first_layer: str = "f16"     # "e4m3": 8-bit first-layer input, per-tensor scale from the batch
     grid: tuple = (0, 0)         # tiles of the whole scene for a snake sweep; (0, 0): the window is the scene
+    view_dirs: bool = False      # colour input [embedding | SH of the ray direction, degrees 0..3]
 
     @property
     def n_slots(self):
@@ -96,6 +97,9 @@ WORKLOADS = {
     "tiny_sweep": Workload("tiny_sweep", (32.0, 32.0, 24.0), 2, 2, 6, 96, CAM_RPC3, (10.0, 30.0),
                            4, 2, 10, 4, 32, 16, True, True, 96, 16, 4, 16, crop_margin=4, dirichlet=True,
                            grid=(3, 3)),
+    "tiny_window_vd": Workload("tiny_window_vd", (48.0, 48.0, 32.0), 2, 2, 6, 64, CAM_RPC3, (10.0, 35.0),
+                               4, 2, 11, 4, 48, 16, True, True, 160, 32, 12, 32, crop_margin=4, dirichlet=True,
+                               view_dirs=True),
     "tiny_window_fp8": Workload("tiny_window_fp8", (48.0, 48.0, 32.0), 2, 2, 6, 64, CAM_RPC3, (10.0, 40.0),
                                 4, 2, 11, 4, 48, 16, True, True, 160, 48, 8, 48, mixed=True, crop_margin=4,
                                 dirichlet=True, scene_kind="blocks", raster=64, first_layer="e4m3"),

@@ -51,7 +51,8 @@ def small_crops(cams, size, seed=0):
 def model_config(w, hidden=64):
     return OS.ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, hidden=hidden,
                           geo_out=w.geo_out, colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots,
-                          K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max, first_layer=w.first_layer)
+                          K_ray=w.K_ray, K_min=w.K_min, K_max=w.K_max, first_layer=w.first_layer,
+                          view_dirs=w.view_dirs)
 
 
 @dataclasses.dataclass

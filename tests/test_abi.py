@@ -56,19 +56,33 @@ def test_model_layout_matches_the_oracle(lib, name):
     assert lay.n_entries == ref.n_entries
     from oracle.step import ModelConfig
     cfg = ModelConfig(L=w.L, F=w.F, log2_T=w.log2_T, n_min=w.n_min, n_max=w.n_max, geo_out=w.geo_out,
-                      colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots)
+                      colour=w.colour, shared_colour=w.shared_colour, n_slots=w.n_slots, view_dirs=w.view_dirs)
     assert lay.tile_params == cfg.tile_params()
     assert lay.n_params == cfg.n_params()
     assert lay.n_optimisers == cfg.n_optimisers()
 
 
 @pytest.mark.parametrize("field,value", [("F", 3), ("L", 5), ("hidden", 32), ("geo_out", 8), ("n_slots", 5),
-                                         ("log2_T", 30), ("precision", 7), ("n_min", 1)])
+                                         ("log2_T", 30), ("precision", 7), ("n_min", 1), ("view_dirs", 1)])
 def test_invalid_models_are_rejected(lib, field, value):
     m = snk.model_struct(8, 2, 14, 16, 256, 4, 0, 1, 1, snk.SNK_FP32)
     setattr(m, field, value)
     out = snk.SnkLayout()
     assert lib.snk_model_layout(ctypes.byref(m), ctypes.byref(out)) == snk.SNK_ERR_INVALID_ARG
+
+
+def test_view_direction_models(lib):
+    """The colour input [g | SH_16(d)] widens V1 by 16 columns; it needs a colour MLP
+    and is not offered with the E4M3 first layer."""
+    out = snk.SnkLayout()
+    plain = snk.model_struct(8, 2, 14, 16, 256, 16, 1, 1, 2, snk.SNK_FP32)
+    vd = snk.model_struct(8, 2, 14, 16, 256, 16, 1, 1, 2, snk.SNK_FP32, view_dirs=True)
+    assert snk.layout(vd).colour_params == snk.layout(plain).colour_params + 64 * 16 == 64 * 32 + 64 * 64 + 3 * 64
+    for prec, flag, ok in [(snk.SNK_MIXED, 1, True), (snk.SNK_MIXED_E4M3, 1, False), (snk.SNK_FP32, 2, False)]:
+        m = snk.model_struct(8, 2, 14, 16, 256, 16, 1, 1, 2, prec)
+        m.view_dirs = flag
+        rc = lib.snk_model_layout(ctypes.byref(m), ctypes.byref(out))
+        assert rc == (snk.SNK_OK if ok else snk.SNK_ERR_INVALID_ARG), (prec, flag)
 
 
 def test_null_arguments_are_rejected_without_a_gpu(lib):

@@ -56,7 +56,7 @@ def mask_flip_deltas(case, ref, wc):
     sample's backward through the unit does, so each flip is one sample's
     contribution recomputed with the other mask, and flips in different samples
     add up."""
-    from oracle import hashgrid, mlp
+    from oracle import hashgrid, mlp, viewdir
     cfg = case.cfg
     smp = ref.smp
     tiles, cols = OS.unflatten(cfg, wc)
@@ -68,10 +68,12 @@ def mask_flip_deltas(case, ref, wc):
             continue
         col = (cols[0] if cfg.shared_colour else cols[k]) if cfg.colour else None
         feat = hashgrid.encode(smp.xyz[idx], tiles[k][0], lay)
-        _, _, acts = mlp.forward(feat, tiles[k][1], col)
+        sh = viewdir.sh16(ref.extra["d"][smp.ray[idx]].astype(np.float64)) if (cfg.view_dirs and col is not None) else None
+        _, _, acts = mlp.forward(feat, tiles[k][1], col, sh)
         layers = [("geo_pre", 0, acts["x0"], tiles[k][1][0]), ("geo_pre", 1, np.maximum(acts["geo_pre"][0], 0), tiles[k][1][1])]
         if col is not None:
-            layers += [("col_pre", 0, acts["g"], col[0]), ("col_pre", 1, np.maximum(acts["col_pre"][0], 0), col[1])]
+            layers += [("col_pre", 0, acts.get("col_in", acts["g"]), col[0]),
+                       ("col_pre", 1, np.maximum(acts["col_pre"][0], 0), col[1])]
         for key, li, h, Wm in layers:
             z = acts[key][li]
             ratio = np.abs(z) / (np.abs(h) @ np.abs(Wm).T + 1e-300)

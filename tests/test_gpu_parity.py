@@ -249,6 +249,8 @@ def test_mlp_forward_and_backward(ctx, name, n_rays):
         acts_abs = dict(acts)
         acts_abs["x0"] = np.abs(acts["x0"])
         acts_abs["g"] = np.abs(acts["g"])
+        if "col_in" in acts:  # the colour layer's input, [g] or [g | SH(d)]
+            acts_abs["col_in"] = np.abs(acts["col_in"])
         ageo, acol, adx = mlp.backward(np.abs(dd[m, 0]), np.abs(dd[m, 1:]), [np.abs(W) for W in tiles[k][1]],
                                        [np.abs(V) for V in col] if col is not None else None, acts_abs)
         for q in range(3):

@@ -172,3 +172,54 @@ def test_truncated_exponential_gradient():
     _, _, acts = mlp.forward(x, [W1, W2, W3], None)
     dgeo, _, dx = mlp.backward(np.ones(2), np.zeros((2, 3)), [W1, W2, W3], None, acts)
     assert np.allclose(dx[:, 0], [np.exp(3.0), np.exp(15.0)], rtol=1e-14)
+
+
+def test_view_direction_encoding_is_an_orthonormal_basis():
+    """The 16 real spherical harmonics of degree <= 3 are orthonormal on the sphere:
+    Gauss-Legendre in z (8 nodes) x 16 equal steps in azimuth integrate their
+    products (degree <= 6) exactly."""
+    from oracle import viewdir
+    zn, zw = np.polynomial.legendre.leggauss(8)
+    phi = np.arange(16) * (2 * np.pi / 16)
+    z = np.repeat(zn, 16)
+    wgt = np.repeat(zw, 16) * (2 * np.pi / 16)
+    p = np.tile(phi, 8)
+    s = np.sqrt(1 - z * z)
+    d = np.stack([s * np.cos(p), s * np.sin(p), z], 1)
+    Y = viewdir.sh16(d)
+    G = (Y * wgt[:, None]).T @ Y
+    assert np.allclose(G, np.eye(16), atol=1e-12)
+    # degree l is odd / even under d -> -d
+    Yn = viewdir.sh16(-d)
+    par = np.array([1] + [-1] * 3 + [1] * 5 + [-1] * 7)
+    assert np.allclose(Yn, Y * par[None, :], atol=1e-13)
+
+
+def test_view_direction_colour_input_gradients_match_central_differences():
+    """Colour MLP on [g | SH(d)]: the colour-weight gradients (including the direction
+    columns of V1) and the embedding gradient are exact derivatives."""
+    from oracle import viewdir
+    rng = np.random.default_rng(4)
+    S, G, H = 7, 16, 16
+    feat = rng.normal(size=(S, 8))
+    geo = [rng.normal(size=(H, 8)) * 0.5, rng.normal(size=(H, H)) * 0.3, rng.normal(size=(G, H)) * 0.3]
+    col = [rng.normal(size=(H, G + 16)) * 0.3, rng.normal(size=(H, H)) * 0.3, rng.normal(size=(3, H)) * 0.3]
+    d = rng.normal(size=(S, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    sh = viewdir.sh16(d)
+    ds, dr = rng.normal(size=S), rng.normal(size=(S, 3))
+
+    def f(cols):
+        s_, r_, _ = mlp.forward(feat, geo, cols, sh)
+        return float((ds * s_).sum() + (dr * r_).sum())
+
+    _, _, acts = mlp.forward(feat, geo, col, sh)
+    dgeo, dcol, dfeat = mlp.backward(ds, dr, geo, col, acts)
+    h = 1e-6
+    for (i, j) in [(0, 3), (5, G + 2), (9, G + 15), (2, 0)]:
+        cp, cm = [c.copy() for c in col], [c.copy() for c in col]
+        cp[0][i, j] += h
+        cm[0][i, j] -= h
+        fd = (f(cp) - f(cm)) / (2 * h)
+        assert abs(fd - dcol[0][i, j]) <= 1e-6 * max(1.0, abs(fd))
+    assert dfeat.shape == (S, 8)
