@@ -47,6 +47,9 @@ def parse():
                     help="also time the binary32 per-tile path on the same workload (mixed runs only)")
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--rays", type=int, default=0, help="override the workload's rays per step (profiling)")
+    ap.add_argument("--sampler-mode", default="segments", choices=["segments", "uniform", "points"],
+                    help="variant: the per-tile segmented sampler, the NeRF-XL uniform distribution, "
+                         "or point samples with backward-difference deltas")
     ap.add_argument("--view-dirs", type=int, default=0,
                     help="variant: colour input [g | SH_16(ray direction)] instead of g")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -72,7 +75,8 @@ def peaks():
 # ---- per-sample algorithmic work (see the design notes) ------------------------
 def mlp_flops_per_sample(w):
     IN, H, G = w.L * w.F, 64, w.geo_out
-    mac = IN * H + H * H + H * G + ((G * H + H * H + H * 3) if w.colour else 0)
+    CIN = G + (16 if w.view_dirs else 0)  # colour input: g, or [g | SH_16(direction)]
+    mac = IN * H + H * H + H * G + ((CIN * H + H * H + H * 3) if w.colour else 0)
     return 2 * mac
 
 
@@ -86,15 +90,19 @@ def field_backward_work(w, precision):
     FP16, 4 B x L*F; the E4M3 path its 1-byte codes); all read xyz (12 B) and
     the upstream gradient (16 B).
     The scatter-add of the table gradient (8 corners x L x F binary32 RMW) goes
-    to L2-resident memory and is reported as l2_red_bytes, not as HBM bytes."""
-    fl = 3 * mlp_flops_per_sample(w)
+    to L2-resident memory and is reported as l2_red_bytes, not as HBM bytes.
+    With view directions the first colour layer's input gradient covers the g
+    columns only (the direction encoding has no parameters behind it), and each
+    sample reads its ray index (4 B; the directions themselves are per ray)."""
+    fl = 3 * mlp_flops_per_sample(w) - (2 * 16 * 64 if w.view_dirs else 0)
+    vd = 4 if w.view_dirs else 0
     if precision == "fp32":
         feat = w.L * 8 * w.F * 4
     elif precision == "mixed_e4m3":
         feat = max(16, w.L * w.F)       # the E4M3 codes, 1 B per feature
     else:
         feat = 4 * max(16, w.L * w.F)
-    return fl, feat + 12 + 16
+    return fl, feat + 12 + 16 + vd
 
 
 def field_forward_work(w, precision):
@@ -102,13 +110,14 @@ def field_forward_work(w, precision):
     (16 B) and, on the mixed path, the split-FP16 features written for the
     backward (4 B x L*F); the table gather (8 corners x L x F) hits the
     L2-resident tables and is reported as l2_gather_bytes."""
+    vd = 4 if w.view_dirs else 0  # the sample's ray index (view-direction colour input)
     if precision == "fp32":
-        return mlp_flops_per_sample(w), 12 + 16
+        return mlp_flops_per_sample(w), 12 + 16 + vd
     if precision == "mixed_e4m3":
         # gather pass: xyz in, binary32 features out; MLP pass: features in, codes and (sigma, rgb) out
         IN = w.L * w.F
         return mlp_flops_per_sample(w), 12 + 4 * IN + 4 * IN + max(16, IN) + 16
-    return mlp_flops_per_sample(w), 12 + 16 + 4 * max(16, w.L * w.F)
+    return mlp_flops_per_sample(w), 12 + 16 + 4 * max(16, w.L * w.F) + vd
 
 
 # DRAM bytes per sample of each kernel measured by ncu (--set full) on the 32768-ray case of the
@@ -362,7 +371,9 @@ def run_ours(args, w):
     ctx = snk.Context(local)
     crops = [torch.from_numpy(t).cuda() for t in targets]
     ctx.set_views(cams, crops)
-    sampler = snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, 1234 + rank, 0)
+    mode = {"segments": snk.SNK_SAMPLE_SEGMENTS, "uniform": snk.SNK_SAMPLE_UNIFORM,
+            "points": snk.SNK_SAMPLE_POINTS}[args.sampler_mode]
+    sampler = snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, 1234 + rank, 0, mode=mode)
     tr = Trainer(ctx, model, snk.window_struct(w.window()), sampler, params)
     batches_h = [W.batch(w, cams, 50 + i + 1000 * rank).view(np.int32) for i in range(N_BATCHES)]
     batches = [torch.from_numpy(b).cuda() for b in batches_h]
@@ -531,6 +542,7 @@ def run_ours(args, w):
                    "parallelism": "replicas" if world > 1 else "single",
                    "launch_shapes": tuning,
                    **({"view_dirs": "SH degrees 0..3 of the ray direction"} if w.view_dirs else {}),
+                   **({"sampler": args.sampler_mode} if args.sampler_mode != "segments" else {}),
                    "l2": "working set per step > L2 (sample buffers %.2f GB)" % (n_samples / args.steps * 52 / 1e9)},
         "rays_per_s": st["n_accepted"] * args.steps / (ms / 1000.0) * world,
         "final_loss": st["loss"], "status": rc,

@@ -195,6 +195,38 @@ def test_view_direction_encoding_is_an_orthonormal_basis():
     assert np.allclose(Yn, Y * par[None, :], atol=1e-13)
 
 
+def test_view_direction_encoding_closed_forms_and_addition_theorem():
+    """Textbook closed forms of all 16 real harmonics (with the graphics-table
+    sign (-1)^m for odd m), and the addition theorem sum_m Y_lm(d)^2 = (2l + 1) / 4 pi,
+    which fixes each degree's normalisation independently of order and sign."""
+    from oracle import viewdir
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    x, y, z = d.T
+    Y = viewdir.sh16(d)
+    pi = np.pi
+    c1 = np.sqrt(3 / (4 * pi))
+    want = {0: np.full_like(x, 0.5 / np.sqrt(pi)),
+            1: -c1 * y, 2: c1 * z, 3: -c1 * x,                                   # (1, -1), (1, 0), (1, 1)
+            4: 0.5 * np.sqrt(15 / pi) * x * y,                                   # (2, -2)
+            6: 0.25 * np.sqrt(5 / pi) * (3 * z * z - 1),                         # (2, 0)
+            8: 0.25 * np.sqrt(15 / pi) * (x * x - y * y),                        # (2, 2)
+            12: 0.25 * np.sqrt(7 / pi) * (5 * z ** 3 - 3 * z),                   # (3, 0)
+            10: 0.5 * np.sqrt(105 / pi) * x * y * z,                             # (3, -2)
+            5: -0.5 * np.sqrt(15 / pi) * y * z, 7: -0.5 * np.sqrt(15 / pi) * x * z,  # (2, -1), (2, 1)
+            9: -0.25 * np.sqrt(35 / (2 * pi)) * y * (3 * x * x - y * y),         # (3, -3)
+            11: -0.25 * np.sqrt(21 / (2 * pi)) * y * (5 * z * z - 1),            # (3, -1)
+            13: -0.25 * np.sqrt(21 / (2 * pi)) * x * (5 * z * z - 1),            # (3, 1)
+            14: 0.25 * np.sqrt(105 / pi) * z * (x * x - y * y),                  # (3, 2)
+            15: -0.25 * np.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y)}        # (3, 3)
+    assert sorted(want) == list(range(16))
+    for j, v in want.items():
+        assert np.allclose(Y[:, j], v, atol=1e-13), j
+    for l in range(4):
+        assert np.allclose((Y[:, l * l:(l + 1) ** 2] ** 2).sum(1), (2 * l + 1) / (4 * pi), atol=1e-13), l
+
+
 def test_view_direction_colour_input_gradients_match_central_differences():
     """Colour MLP on [g | SH(d)]: the colour-weight gradients (including the direction
     columns of V1) and the embedding gradient are exact derivatives."""
