@@ -83,9 +83,10 @@ def albedo(hf, x, y):
             + A[i0, j0 + 1] * (1 - fv) * fu + A[i0 + 1, j0 + 1] * fv * fu)
 
 
-def shade_rays(hf, top, d, step=1.0):
-    """Colour (n, 3) of rays starting at `top` (scene coordinates, z = z_max)
-    with unit directions d, against heightfield hf inside its box."""
+def _first_hit(hf, top, d, step):
+    """March each ray from `top` in steps of about `step` metres of height to the
+    first sign change of z - height, then bisect to 1e-9 m.  Returns (found mask,
+    lo, hi) with the hit bracketed in [lo, hi] for the found rays."""
     n = top.shape[0]
     z_len = hf.hi[2] - hf.lo[2]
     t_max = z_len / np.maximum(-d[:, 2], 1e-12)
@@ -119,6 +120,28 @@ def shade_rays(hf, top, d, step=1.0):
         below = f <= 0
         hi = np.where(below, mid, hi)
         lo = np.where(below, lo, mid)
+    return found, lo, hi
+
+
+def surface_t(hf, top, d, step=1.0):
+    """Distance (n,) from `top` along d to the first surface hit inside the box, NaN
+    for rays that miss (the depth a perfect model renders with opacity 1)."""
+    found, lo, hi = _first_hit(hf, top, d, step)
+    t = np.full(top.shape[0], np.nan)
+    if lo.size:
+        p = top[found] + hi[:, None] * d[found]
+        inside = ((p[:, 0] >= hf.lo[0]) & (p[:, 0] <= hf.hi[0]) & (p[:, 1] >= hf.lo[1]) & (p[:, 1] <= hf.hi[1]))
+        t[np.flatnonzero(found)[inside]] = hi[inside]
+    return t
+
+
+def shade_rays(hf, top, d, step=1.0):
+    """Colour (n, 3) of rays starting at `top` (scene coordinates, z = z_max)
+    with unit directions d, against heightfield hf inside its box."""
+    n = top.shape[0]
+    found, lo, hi = _first_hit(hf, top, d, step)
+    tp = top[found]
+    dd = d[found]
     out = np.zeros((n, 3))
     if lo.size:
         p = tp + hi[:, None] * dd

@@ -98,3 +98,7 @@ def test_target_renderer_flat_ground_closed_form():
     expect = OT.albedo(hf, p[:, 0], p[:, 1]) * (0.2 + 0.8 * hf.sun[2])
     assert inside.any()
     assert np.allclose(col[inside], expect[inside], atol=1e-7)
+    # the hit distance itself (the depth a perfect model renders), NaN outside the box
+    t = OT.surface_t(hf, o, d)
+    assert np.allclose(t[inside], t_hit[inside], rtol=0, atol=1e-8)
+    assert np.all(np.isnan(t[~inside]))
