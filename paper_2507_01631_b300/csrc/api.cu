@@ -767,7 +767,7 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
 
 static bool tuning_ok(const snk_tuning &t) {
   auto mult32 = [](int v, int lo, int hi) { return v >= lo && v <= hi && v % 32 == 0; };
-  return (t.tc_fwd_ctas == 1 || t.tc_fwd_ctas == 2) && (t.tc_fwd_levels == 1 || t.tc_fwd_levels == 2) &&
+  return (t.tc_fwd_ctas >= 1 && t.tc_fwd_ctas <= 3) && (t.tc_fwd_levels == 1 || t.tc_fwd_levels == 2) &&
          (t.fp32_ctas == 1 || t.fp32_ctas == 2) && mult32(t.composite_threads, 64, 512) &&
          mult32(t.sampler_threads, 128, 512);
 }
@@ -886,9 +886,10 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
     if (model->precision != SNK_FP32) {
       best = -1.0;
       int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels;
-      for (int c : {1, 2})
+      for (int c : {1, 2, 3})
         for (int l : {1, 2}) {
           if (l == 2 && model->precision == SNK_MIXED_E4M3) continue;  // no gather in that forward
+          if (l == 2 && c == 3) continue;                              // three CTAs: one level at a time
           ctx->tune.tc_fwd_ctas = c;
           ctx->tune.tc_fwd_levels = l;
           const double ms = time([&] { return field(kForward); }, 2);

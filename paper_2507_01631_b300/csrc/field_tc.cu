@@ -69,22 +69,26 @@ struct L {
   static constexpr int DB = BWD ? DA + TM * 64 * 2 : 0;        // [128 x 64]
   static constexpr int DG = BWD ? DB + TM * 64 * 2 : 0;        // [128 x 16]
   static constexpr int D3 = BWD ? DG + TM * 16 * 2 : 0;        // [128 x 16]
-  // low parts (x 2^11): of the forward operands while the forward runs, then of the deltas
+  // Low parts (x 2^11): of the forward operands while the forward runs, then of the deltas.
+  // The forward keeps one [128 x 64] buffer for every operand (hi and lo): a layer's epilogue
+  // runs only after the MMA that read the layer's input has completed, so the output can
+  // overwrite it.  The backward keeps every activation for its weight-gradient MMAs.
   static constexpr int LO = BWD ? D3 + TM * 16 * 2 : 0;
   static constexpr int XL0 = LO;                               // [128 x INP] features
-  static constexpr int XLA = XL0 + TM * INP * 2;               // [128 x 64] h1, then c1
-  static constexpr int XLB = XLA + TM * 64 * 2;                // [128 x 64] h2, then g, then c2
+  static constexpr int XLA = BWD ? XL0 + TM * INP * 2 : LO;    // [128 x 64] h1, then c1
+  static constexpr int XLB = BWD ? XLA + TM * 64 * 2 : LO;     // [128 x 64] h2, then g, then c2
   static constexpr int XL3 = XLB;
   static constexpr int DAL = LO, DBL = LO + TM * 64 * 2, DGL = LO + 2 * TM * 64 * 2, D3L = DGL + TM * 16 * 2;
-  static constexpr int LO_END = LO + cmax(TM * INP * 2 + 2 * TM * 64 * 2, 2 * TM * 64 * 2 + 2 * TM * 16 * 2);
+  static constexpr int LO_END =
+      LO + (BWD ? cmax(TM * INP * 2 + 2 * TM * 64 * 2, 2 * TM * 64 * 2 + 2 * TM * 16 * 2) : TM * 64 * 2);
   // high parts of the forward operands
   static constexpr int X0 = LO_END;                            // [128 x INP]
-  static constexpr int X1 = X0 + TM * INP * 2;                 // h1  [128 x 64]
-  static constexpr int X2 = X1 + TM * 64 * 2;                  // h2
-  static constexpr int X3 = BWD ? X2 + TM * 64 * 2 : X2;       // g [128 x CIN] (forward: h2's buffer)
-  static constexpr int X4 = BWD ? X3 + TM * CIN * 2 : X1;      // c1 (forward: h1's buffer)
-  static constexpr int X5 = BWD ? X4 + TM * 64 * 2 : X2;       // c2 (forward: h2's buffer)
-  static constexpr int W1 = BWD ? X5 + TM * 64 * 2 : X2 + TM * 64 * 2;  // [64 x INP]
+  static constexpr int X1 = BWD ? X0 + TM * INP * 2 : X0;      // h1  [128 x 64]
+  static constexpr int X2 = BWD ? X1 + TM * 64 * 2 : X0;       // h2
+  static constexpr int X3 = BWD ? X2 + TM * 64 * 2 : X0;       // g [128 x CIN]
+  static constexpr int X4 = BWD ? X3 + TM * CIN * 2 : X0;      // c1
+  static constexpr int X5 = BWD ? X4 + TM * 64 * 2 : X0;       // c2
+  static constexpr int W1 = BWD ? X5 + TM * 64 * 2 : X0 + TM * 64 * 2;  // [64 x INP]
   static constexpr int W2 = W1 + 64 * INP * 2;                 // [64 x 64]
   static constexpr int W3 = W2 + 64 * 64 * 2;                  // [16 x 64]
   static constexpr int V1 = W3 + 16 * 64 * 2;                  // [64 x CIN]
@@ -236,8 +240,8 @@ struct TileInfo {
   int32_t n_valid;  // rows 0 .. n_valid-1 are samples of the slot
 };
 
-template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD>
-__global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(const FieldArgs a) {
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB>
+__global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const FieldArgs a) {
   using Y = L<IN, BWD, VD>;
   constexpr int INP = Y::INP;
   constexpr int CIN = Y::CIN;
@@ -520,6 +524,15 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
               pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
         }
       }
+      if (IN < INP && half == 0) {
+        // padding columns of the first layer's K: the shared operand buffer held the last
+        // tile's activations there
+#pragma unroll
+        for (int c = IN; c < INP; c += 2) {
+          *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, c, TM)) = 0u;
+          *reinterpret_cast<uint32_t *>(sm + Y::XL0 + tc::core_off(s, c, TM)) = 0u;
+        }
+      }
       tc::bar_sync(kChainBar, TT);
       // the tile's features (high and low parts), in the shared-memory layout, for the backward
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
@@ -775,13 +788,14 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, BWD ? 1 : 2) k_field_tc(co
   if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
 }
 
-template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD>
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB>
 cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_ctas) {
   using Y = L<IN, BWD, VD>;
   static_assert(Y::SMEM <= 232448, "shared memory per CTA");
-  static_assert(BWD || 2 * (Y::SMEM + 1024) <= 233472, "two forward CTAs per SM");
+  static_assert(MINB * (Y::SMEM + 1024) <= 233472, "resident CTAs per SM: shared memory");
+  static_assert(MINB * Y::TCOLS <= 512, "resident CTAs per SM: tensor memory");
   static_assert(Y::C_V1 + Y::CIN <= Y::C_DL || !BWD, "tensor-memory columns of dV1");
-  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL, VD>;
+  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL, VD, MINB>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
@@ -800,17 +814,22 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_
 
 template <int IN, int G, bool COL, bool Q8, bool VD>
 cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
-  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8, 1, VD>(a, sm_count, st, 1);
+  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8, 1, VD, 1>(a, sm_count, st, 1);
+  // three CTAs per SM: compiled for 85 registers a thread, one level of corner loads at a time
+  if (tu.tc_fwd_ctas == 3) return launch_t<IN, G, COL, false, Q8, 1, VD, 3>(a, sm_count, st, 3);
   // the E4M3 forward reads its features instead of gathering them: no gather shape to pick
-  if (!Q8 && tu.tc_fwd_levels == 2) return launch_t<IN, G, COL, false, Q8, 2, VD>(a, sm_count, st, tu.tc_fwd_ctas);
-  return launch_t<IN, G, COL, false, Q8, 1, VD>(a, sm_count, st, tu.tc_fwd_ctas);
+  if (!Q8 && tu.tc_fwd_levels == 2)
+    return launch_t<IN, G, COL, false, Q8, 2, VD, 2>(a, sm_count, st, tu.tc_fwd_ctas);
+  return launch_t<IN, G, COL, false, Q8, 1, VD, 2>(a, sm_count, st, tu.tc_fwd_ctas);
 }
 
 template <int IN, int G, bool COL>
 cudaError_t launch_q(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
-  if (COL && a.m.view_dirs) {
-    if (a.m.e4m3 || a.smp_ray == nullptr || a.ray_od == nullptr || a.n_rays < 1) return cudaErrorInvalidValue;
-    return launch_mode<IN, G, COL, false, true>(a, sm_count, st, tu);
+  if constexpr (COL) {
+    if (a.m.view_dirs) {
+      if (a.m.e4m3 || a.smp_ray == nullptr || a.ray_od == nullptr || a.n_rays < 1) return cudaErrorInvalidValue;
+      return launch_mode<IN, G, COL, false, true>(a, sm_count, st, tu);
+    }
   }
   if (a.m.e4m3) return launch_mode<IN, G, COL, true, false>(a, sm_count, st, tu);
   return launch_mode<IN, G, COL, false, false>(a, sm_count, st, tu);

@@ -6,7 +6,7 @@ namespace snk {
 
 // Launch shapes picked by snk_autotune (defaults: the measured best on the 2x2 window).
 struct Tuning {
-  int tc_fwd_ctas = 2;          // tensor-core forward: persistent CTAs per SM (1, 2)
+  int tc_fwd_ctas = 3;          // tensor-core forward: persistent CTAs per SM (1, 2, 3)
   int tc_fwd_levels = 1;        // tensor-core forward: levels whose corner loads are issued together (1, 2)
   int fp32_ctas = 2;            // binary32 field kernels: persistent CTAs per SM (1, 2)
   int composite_threads = 256;  // compositing: threads per block (64 .. 512, multiple of 32)

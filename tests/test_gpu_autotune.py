@@ -12,7 +12,7 @@ from gpu_util import make_case, normwise
 
 pytestmark = pytest.mark.gpu
 DEFAULT = dict(tc_fwd_ctas=2, tc_fwd_levels=1, fp32_ctas=2, composite_threads=256, sampler_threads=256)
-ALTERNATIVES = [("tc_fwd_ctas", 1), ("tc_fwd_levels", 2), ("fp32_ctas", 1), ("composite_threads", 64),
+ALTERNATIVES = [("tc_fwd_ctas", 1), ("tc_fwd_ctas", 3), ("tc_fwd_levels", 2), ("fp32_ctas", 1), ("composite_threads", 64),
                 ("composite_threads", 512), ("sampler_threads", 128), ("sampler_threads", 512)]
 
 
@@ -67,7 +67,7 @@ def test_autotune_picks_valid_shapes_and_leaves_the_training_state(ctx, precisio
     t = tr.autotune(dev(case.pix.view(np.int32)))
     torch.cuda.synchronize()
     assert t["tuned"] == 1
-    assert t["tc_fwd_ctas"] in (1, 2) and t["tc_fwd_levels"] in (1, 2) and t["fp32_ctas"] in (1, 2)
+    assert t["tc_fwd_ctas"] in (1, 2, 3) and t["tc_fwd_levels"] in (1, 2) and t["fp32_ctas"] in (1, 2)
     assert t["composite_threads"] in (64, 128, 256, 512) and t["sampler_threads"] in (128, 256, 512)
     assert ctx.tuning() == t
     for a, b in zip(before, (tr.params, tr.grads, tr.m, tr.v, tr.steps, tr.state)):
@@ -80,7 +80,7 @@ def test_autotune_picks_valid_shapes_and_leaves_the_training_state(ctx, precisio
 
 
 def test_out_of_range_tuning_is_rejected(ctx):
-    for key, val in [("tc_fwd_ctas", 3), ("tc_fwd_levels", 4), ("composite_threads", 96 + 1),
+    for key, val in [("tc_fwd_ctas", 4), ("tc_fwd_levels", 4), ("composite_threads", 96 + 1),
                      ("sampler_threads", 1024), ("fp32_ctas", 0)]:
         with pytest.raises(RuntimeError):
             ctx.set_tuning(**dict(DEFAULT, **{key: val}))
