@@ -378,7 +378,7 @@ def run_ours(args, w):
     batches_h = [W.batch(w, cams, 50 + i + 1000 * rank).view(np.int32) for i in range(N_BATCHES)]
     batches = [torch.from_numpy(b).cuda() for b in batches_h]
     nseg = 1 + (w.nx == 2) + (w.ny == 2)
-    ctx.reserve(w.n_rays, w.n_rays * nseg * w.K_max + 512)
+    ctx.reserve(w.n_rays, ctx.max_samples(snk.window_struct(w.window()), sampler, w.n_rays))
     stream = torch.cuda.current_stream()
 
     # launch shapes: picked on the first batch, outside the timed region

@@ -218,6 +218,13 @@ int snk_ctx_create(int device, snk_ctx **out);
 int snk_ctx_destroy(snk_ctx *ctx);
 /* Size the workspace for batches of up to max_rays rays and max_samples samples. */
 int snk_ctx_reserve(snk_ctx *ctx, int64_t max_rays, int64_t max_samples);
+/* Host only: the sample capacity a step of B rays with this window and sampler
+ * sizes its workspace for (an upper bound of the batch's samples, Sec. 4.5:
+ * K_ray a ray in uniform mode, else at most max(s K_min, (s - 1) K_min + K_ray)
+ * + s and at most s K_max for a window whose rays have up to s segments, plus
+ * slot alignment), so that snk_ctx_reserve(ctx, B, snk_max_samples(...)) sizes
+ * the context once before graph capture.  Returns -1 for a NULL argument. */
+int64_t snk_max_samples(const snk_window *win, const snk_sampler *sampler, int64_t B);
 /* Message of the last failing call on ctx (static storage of the context). */
 const char *snk_last_error(const snk_ctx *ctx);
 /* Library version string (host, static). */
@@ -429,7 +436,13 @@ typedef struct {
     int32_t composite_threads; /* compositing kernel: threads per block, 64..512, multiple of 32 */
     int32_t sampler_threads;   /* ray and sample kernels: threads per block, 128..512, multiple of 32 */
     int32_t tuned;             /* out: 1 if the values came from snk_autotune */
-    int32_t reserved[2];
+    int32_t tc_bwd_saved;      /* tensor-core training step: 1 (default) the forward stores each layer's
+                                  activations (FP16 high parts, 544 B a sample with a colour network, 576 B
+                                  with view directions, 256 B without) in a context-owned buffer sized for
+                                  the reserved samples, and the backward copies them back instead of
+                                  recomputing the forward; 0 the backward recomputes them.  Same results
+                                  either way (up to the order of float atomics). */
+    int32_t reserved;
 } snk_tuning;
 
 /* Current launch shapes of ctx (defaults until tuned or set). */

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include <algorithm>
 #include <atomic>
 #include <vector>
 
@@ -35,6 +36,8 @@ struct snk_ctx {
   size_t pool_ws_bytes = 0;
   void *occ_ws = nullptr;      // occupancy update scratch: state | per-block partial sums | thresholds
   size_t occ_ws_bytes = 0;
+  void *acts = nullptr;        // stored activations of a tensor-core training step (tc_bwd_saved)
+  size_t acts_bytes = 0;
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -304,9 +307,40 @@ int ensure_ws(snk_ctx *ctx, int64_t B, int64_t S) {
   return SNK_OK;
 }
 
+// Samples of a batch of B rays at most.  Uniform mode: K_ray a ray.  Otherwise a ray's segments
+// take K = clamp(rint(K_ray len_seg / len_ray), K_min, K_max) each: the segments above K_min share
+// at most K_ray (plus 1/2 of rounding each and a few binary32 ulps of the shares' sum), so a ray
+// holds at most max(segs K_min, (segs - 1) K_min + K_ray) + segs samples, and segs K_max.  A batch
+// that still overflowed would set the status check bit and produce no samples.
 int64_t max_samples_for(const snk_window *w, const snk_sampler *s, int64_t B) {
-  const int segs = 1 + (w->nx == 2 ? 1 : 0) + (w->ny == 2 ? 1 : 0);
-  return B * segs * (int64_t)s->K_max + (int64_t)kSlotAlign * kMaxSlots;
+  const int64_t segs = 1 + (w->nx == 2 ? 1 : 0) + (w->ny == 2 ? 1 : 0);
+  int64_t per_ray = s->K_ray;
+  if (s->mode != kSampleUniform) {
+    const int64_t shares = std::max<int64_t>(segs * s->K_min, (segs - 1) * s->K_min + s->K_ray) + segs;
+    per_ray = std::min<int64_t>(segs * s->K_max, shares);
+  }
+  return B * per_ray + (int64_t)kSlotAlign * kMaxSlots;
+}
+
+// The stored-activation buffer of a tensor-core training step for the context's sample capacity.
+int ensure_acts(snk_ctx *ctx, const snk_model *model, cudaStream_t st) {
+  const size_t need = (size_t)(ctx->cap_samples / 128 + 1) * (size_t)act_tile_bytes(model->colour != 0, model->view_dirs != 0);
+  if (need <= ctx->acts_bytes) return SNK_OK;
+  if (ctx->acts) {
+    SNK_CK(ctx, cudaStreamSynchronize(st));
+    SNK_CK(ctx, cudaFree(ctx->acts));
+    ctx->acts = nullptr;
+    ctx->acts_bytes = 0;
+  }
+  if (cudaMalloc(&ctx->acts, need) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->acts = nullptr;
+    return fail(ctx, SNK_ERR_OOM,
+                "stored activations of %zu bytes could not be allocated: reserve fewer samples or set "
+                "tc_bwd_saved = 0 (snk_set_tuning)", need);
+  }
+  ctx->acts_bytes = need;
+  return SNK_OK;
 }
 
 int prepare(snk_ctx *ctx, const snk_model *model, snk_layout *lay, ModelDev *md) {
@@ -331,6 +365,11 @@ int check_params(snk_ctx *ctx, const snk_model *model, const snk_params *p, bool
 extern "C" {
 
 const char *snk_version(void) { return "libsnk 0.1 (sm_103a)"; }
+
+int64_t snk_max_samples(const snk_window *win, const snk_sampler *sampler, int64_t B) {
+  if (!win || !sampler || B < 0) return -1;
+  return max_samples_for(win, sampler, B);
+}
 
 int snk_abi_sizes(int64_t *sizes, int n) {
   const int64_t all[9] = {(int64_t)sizeof(snk_camera), (int64_t)sizeof(snk_window), (int64_t)sizeof(snk_model),
@@ -377,6 +416,7 @@ int snk_ctx_destroy(snk_ctx *ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->pool_ws) cudaFree(ctx->pool_ws);
   if (ctx->occ_ws) cudaFree(ctx->occ_ws);
+  if (ctx->acts) cudaFree(ctx->acts);
   if (ctx->d_views) cudaFree(ctx->d_views);
   if (ctx->h_views) cudaFreeHost(ctx->h_views);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -602,8 +642,9 @@ static RayBuffers step_rays(const snk_ctx *ctx, const snk_model *model) {
 
 // n_rays: the batch size of the rays whose directions ray_od holds ([6][n_rays]); every
 // sample's ray index (rb.smp_ray) is below it.
+// train: a training step (its forward stores activations for its backward when tc_bwd_saved).
 static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, const snk_params *p,
-                     const snk_state *state, int mode, cudaStream_t st, int n_rays) {
+                     const snk_state *state, int mode, cudaStream_t st, int n_rays, bool train) {
   FieldArgs fa{};
   fa.m = md;
   fa.params = p->params;
@@ -624,6 +665,11 @@ static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, c
   fa.n_rays = n_rays;
   if (model->precision != SNK_FP32) {
     fa.slot_only = -1;
+    if (train && ctx->tune.tc_bwd_saved) {
+      int rc = ensure_acts(ctx, model, st);
+      if (rc) return rc;
+      fa.acts = static_cast<uint16_t *>(ctx->acts);
+    }
     if (md.e4m3 && mode == kForward) {
       // the per-slot scales need every feature of the batch first
       SNK_CK(ctx, cudaMemsetAsync(ctx->amax, 0, sizeof(uint32_t) * kMaxSlots, st));
@@ -666,7 +712,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   }
   {
     StageMark m(ctx, 1, st);
-    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B, true))) return rc;
   }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
@@ -687,7 +733,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   }
   {
     StageMark m(ctx, 3, st);
-    if ((rc = run_field(ctx, model, md, p, state, kBackward, st, B))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kBackward, st, B, true))) return rc;
   }
   AdamArgs aa{};
   aa.params = p->params;
@@ -747,7 +793,7 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   }
   {
     StageMark m(ctx, 1, st);
-    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B, false))) return rc;
   }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
@@ -768,6 +814,7 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
 static bool tuning_ok(const snk_tuning &t) {
   auto mult32 = [](int v, int lo, int hi) { return v >= lo && v <= hi && v % 32 == 0; };
   return (t.tc_fwd_ctas >= 1 && t.tc_fwd_ctas <= 3) && (t.tc_fwd_levels == 1 || t.tc_fwd_levels == 2) &&
+         (t.tc_bwd_saved == 0 || t.tc_bwd_saved == 1) &&
          (t.fp32_ctas == 1 || t.fp32_ctas == 2) && mult32(t.composite_threads, 64, 512) &&
          mult32(t.sampler_threads, 128, 512);
 }
@@ -776,6 +823,7 @@ static void to_abi(const snk::Tuning &u, bool tuned, snk_tuning *t) {
   t->tc_fwd_ctas = u.tc_fwd_ctas;
   t->tc_fwd_levels = u.tc_fwd_levels;
   t->fp32_ctas = u.fp32_ctas;
+  t->tc_bwd_saved = u.tc_bwd_saved;
   t->composite_threads = u.composite_threads;
   t->sampler_threads = u.sampler_threads;
   t->tuned = tuned ? 1 : 0;
@@ -793,6 +841,7 @@ int snk_set_tuning(snk_ctx *ctx, const snk_tuning *in) {
   ctx->tune.tc_fwd_ctas = in->tc_fwd_ctas;
   ctx->tune.tc_fwd_levels = in->tc_fwd_levels;
   ctx->tune.fp32_ctas = in->fp32_ctas;
+  ctx->tune.tc_bwd_saved = in->tc_bwd_saved;
   ctx->tune.composite_threads = in->composite_threads;
   ctx->tune.sampler_threads = in->sampler_threads;
   ctx->tuned = false;
@@ -852,7 +901,7 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
       return fail(ctx, SNK_ERR_CUDA, "snk_autotune: sampling failed");
     return SNK_OK;
   };
-  auto field = [&](int mode) { return run_field(ctx, model, md, &ps, state, mode, st, B); };
+  auto field = [&](int mode) { return run_field(ctx, model, md, &ps, state, mode, st, B, true); };
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
   ca.smp_t = ctx->rb.smp_t;
@@ -884,21 +933,35 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
     if (sample() != SNK_OK) break;  // leave this batch's samples in the workspace
     // field kernels
     if (model->precision != SNK_FP32) {
-      best = -1.0;
-      int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels;
-      for (int c : {1, 2, 3})
-        for (int l : {1, 2}) {
-          if (l == 2 && model->precision == SNK_MIXED_E4M3) continue;  // no gather in that forward
-          if (l == 2 && c == 3) continue;                              // three CTAs: one level at a time
-          ctx->tune.tc_fwd_ctas = c;
-          ctx->tune.tc_fwd_levels = l;
-          const double ms = time([&] { return field(kForward); }, 2);
-          if (ms < 0) break;
-          if (best < 0 || ms < best) best = ms, pc = c, pl = l;
-        }
+      // per backward mode (stored activations when their buffer can be had, recompute): the
+      // fastest forward shape, then forward + backward decide between the modes
+      double best_step = -1.0;
+      snk::Tuning pick = ctx->tune;
+      for (int sv : {1, 0}) {
+        if (sv == 1 && ensure_acts(ctx, model, st) != SNK_OK) continue;  // no room: recompute only
+        ctx->tune.tc_bwd_saved = sv;
+        best = -1.0;
+        int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels;
+        for (int c : {1, 2, 3})
+          for (int l : {1, 2}) {
+            if (l == 2 && model->precision == SNK_MIXED_E4M3) continue;  // no gather in that forward
+            if (l == 2 && c == 3) continue;                              // three CTAs: one level at a time
+            ctx->tune.tc_fwd_ctas = c;
+            ctx->tune.tc_fwd_levels = l;
+            const double ms = time([&] { return field(kForward); }, 2);
+            if (ms < 0) break;
+            if (best < 0 || ms < best) best = ms, pc = c, pl = l;
+          }
+        if (rc) break;
+        ctx->tune.tc_fwd_ctas = pc;
+        ctx->tune.tc_fwd_levels = pl;
+        if (field(kForward) != SNK_OK) break;  // this mode's forward outputs for its backward
+        const double b = time([&] { return field(kBackward); }, 1);
+        if (b < 0) break;
+        if (best_step < 0 || best + b < best_step) best_step = best + b, pick = ctx->tune;
+      }
       if (rc) break;
-      ctx->tune.tc_fwd_ctas = pc;
-      ctx->tune.tc_fwd_levels = pl;
+      ctx->tune = pick;
     } else {
       best = -1.0;
       int pc = saved.fp32_ctas;
@@ -1030,7 +1093,7 @@ int snk_occupancy_update(snk_ctx *ctx, const snk_model *model, const snk_params 
   const cudaStream_t st = (cudaStream_t)stream;
   SNK_CK(ctx, cudaMemsetAsync(state, 0, sizeof(snk_state), st));
   SNK_CK(ctx, launch_occ_points(model->n_slots, R, seed, step, ctx->rb.smp_xyz, ctx->rb.smp_ray, state, st));
-  if ((rc = run_field(ctx, model, md, p, state, kForward, st, 1))) return rc;
+  if ((rc = run_field(ctx, model, md, p, state, kForward, st, 1, false))) return rc;
   SNK_CK(ctx, launch_occ_update(model->n_slots, R, ctx->sigma_rgb, decay, threshold, density, occupancy, partial, thr,
                                 st));
   return SNK_OK;

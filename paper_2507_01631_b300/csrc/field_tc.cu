@@ -11,8 +11,9 @@
 // global memory (64 bytes per sample) so that the backward does not re-gather
 // 512 bytes per sample from the tables.
 //
-// Backward (per tile, one CTA per SM): warps 0-7 reload the features,
-// recompute the MLP activations, then per layer two MMAs: the input gradient
+// Backward (per tile, one CTA per SM): warps 0-7 reload the features and
+// either recompute the MLP activations or (a training step whose forward stored
+// them) copy them back with bulk copies, then per layer two MMAs: the input gradient
 // dX = delta * W (W read MN-major from the same shared buffer the forward
 // reads K-major) and the weight gradient dW += delta^T * X (both operands read
 // MN-major from the sample-major buffers; the output rows of dW are padded to
@@ -20,8 +21,9 @@
 // tensor memory for the whole persistent loop and are added to the FP32
 // gradient buffer when the CTA moves to another slot and at exit.  The
 // feature gradient of a tile goes through a two-buffer shared-memory ring to
-// warps 8-11, which scatter-add it into the FP32 table gradients with
-// fire-and-forget reductions (one thread per sample; x-adjacent corners that
+// the scatter warps (4, or 8 with stored activations), which scatter-add it into
+// the FP32 table gradients with fire-and-forget reductions (one thread per sample
+// and level group; x-adjacent corners that
 // share an aligned pair of entries in one 16-byte reduction) while warps 0-7
 // run the next tile's MMA chain: the L1 reduction traffic of one tile overlaps
 // the tensor-core latency chain of the next.
@@ -46,7 +48,11 @@ namespace {
 
 constexpr int TM = 128;  // samples per tile = MMA M
 constexpr int TT = 256;  // threads of the MMA / epilogue warps (warps 0-7)
-constexpr int TS = 128;  // backward: threads of the scatter warps (warps 8-11), one per sample of a tile
+// Backward: threads of the scatter warps (warps 8..), one per sample of a tile and level
+// group: 4 warps (every level of a sample) when the MMA warps recompute the forward, 8 warps
+// (even / odd levels) when they read stored activations -- their chain is then short
+// enough that the scatter binds, and a second thread per sample shortens it.
+__host__ __device__ constexpr int scatter_threads(bool sv) { return sv ? 256 : 128; }
 constexpr uint32_t kChainBar = 1;  // named barrier of the 256 MMA / epilogue threads
 // Split FP16 operands (Markidis et al. 2018): every activation and delta x
 // that feeds an MMA is carried as hi = fp16(x) and lo = fp16((x - hi) * 2^11);
@@ -107,6 +113,11 @@ struct L {
   // tensor-memory columns: 0..63 accumulator of the high parts; C_DL the low parts
   static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
   static constexpr uint32_t C_DL = BWD ? 448 : 64;
+  // Stored activations of a tile (high parts, FP16, in the layout above), written by the
+  // forward of a training step and copied back by the backward instead of recomputed:
+  // h1, h2 [128 x 64], then with a colour network g [128 x CIN], c1, c2 [128 x 64].
+  static constexpr int A1 = 0, A2 = TM * 64 * 2, A3 = 2 * TM * 64 * 2, A4 = A3 + TM * CIN * 2, A5 = A4 + TM * 64 * 2;
+  __host__ __device__ static constexpr int act_bytes(bool col) { return col ? A5 + TM * 64 * 2 : A3; }
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
@@ -157,9 +168,11 @@ __device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, 
 // [128 x 64] activation buffer).  v is written as hi (out) and scaled lo (out_lo).
 // LO = false: the layer had no low-part MMA (E4M3 first layer, whose input is exact in
 // FP16); scale multiplies the sum (the E4M3 input's per-slot scale, else 1).
+// gout (nullable): a global copy of the high parts in the same layout (stored activations).
 template <int MODE, bool LO = true>
 __device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t *out, uint8_t *out_lo,
-                                      const uint8_t *mask, int r, int ch, float scale = 1.0f) {
+                                      const uint8_t *mask, int r, int ch, float scale = 1.0f,
+                                      uint8_t *gout = nullptr) {
   float v[32];
   {
     float a[16], b[16], c[16], d[16];
@@ -201,6 +214,7 @@ __device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t
     }
     *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
     *reinterpret_cast<uint4 *>(out_lo + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+    if (gout) *reinterpret_cast<uint4 *>(gout + off) = make_uint4(o[0], o[1], o[2], o[3]);
   }
 }
 
@@ -215,8 +229,9 @@ __device__ __forceinline__ void ld16_pair(uint32_t taddr, uint32_t taddr_lo, flo
 }
 
 // Store 16 floats as one FP16 row segment of a [128 x 16] buffer (and, if buf_lo is
-// given, their scaled low parts).
-__device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, const float (&v)[16]) {
+// given, their scaled low parts; if gbuf is given, a global copy of the high parts).
+__device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, const float (&v)[16],
+                                        uint8_t *gbuf = nullptr) {
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     uint32_t o[4], ol[4];
@@ -228,6 +243,7 @@ __device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, co
     }
     *reinterpret_cast<uint4 *>(buf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
     if (buf_lo) *reinterpret_cast<uint4 *>(buf_lo + tc::core_off(r, q * 8, TM)) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+    if (gbuf) *reinterpret_cast<uint4 *>(gbuf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
   }
 }
 
@@ -240,18 +256,23 @@ struct TileInfo {
   int32_t n_valid;  // rows 0 .. n_valid-1 are samples of the slot
 };
 
-template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB>
-__global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const FieldArgs a) {
+// SV (backward): the forward stored the tile's activations (a.acts); they are copied back
+// with bulk copies instead of recomputed.
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB, bool SV>
+__global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_field_tc(const FieldArgs a) {
   using Y = L<IN, BWD, VD>;
   constexpr int INP = Y::INP;
   constexpr int CIN = Y::CIN;
+  constexpr int ACT = Y::act_bytes(COL);
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + Y::MISC);
   uint64_t *full = mbar + 1;   // [2] the MMA warps filled DF[b] (TT arrivals)
+  constexpr int TS = scatter_threads(SV);
   uint64_t *empty = mbar + 3;  // [2] the scatter warps drained DF[b] (TS arrivals)
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Y::MISC + 40);
   TileInfo *info = reinterpret_cast<TileInfo *>(sm + Y::MISC + 48);  // [2]
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Y::MISC + 80);
+  uint64_t *abar = reinterpret_cast<uint64_t *>(sm + Y::MISC + 88);  // stored activations landed
   float *dfbuf = reinterpret_cast<float *>(sm + Y::DF);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int r = 32 * (warp & 3) + lane;  // TMEM lane = tile row of this thread
@@ -271,6 +292,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
       }
     }
     *abort_flag = 0;
+    if (SV) tc::mbar_init(abar, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, Y::TCOLS);
@@ -281,8 +303,8 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-  uint32_t phase = 0;
-  bool abort = false;
+  uint32_t phase = 0, aphase = 0;
+  bool abort = false, a_pending = false;
 
   int64_t r0 = 0, r1 = st->slot_base[kMaxSlots];
   if (a.slot_only >= 0) {
@@ -345,9 +367,9 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
 
   if (BWD && t >= TT) {
     // ---- scatter warps: add each tile's feature gradient, weighted by the trilinear
-    // weights, into the FP32 table gradients (float2 reductions, one thread per sample);
-    // they run while the MMA warps work on the next tile ----
-    const int s = t - TT;
+    // weights, into the FP32 table gradients (float2 reductions, one thread per sample and
+    // level group); they run while the MMA warps work on the next tile ----
+    const int s = (t - TT) % TM, lq = (t - TT) / TM;  // sample of the tile, level group
     int j = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       if (slot_of(st, r0 + tile * TM) < 0) continue;  // the MMA warps skip the same tiles
@@ -368,7 +390,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
         for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[idx * 3 + q];
         const float *dfr = dfbuf + (b * TM + s) * Y::DFS;
         float2 *gt0 = reinterpret_cast<float2 *>(a.grads + (int64_t)ti.slot * m.tile_params);
-        for (int l = 0; l < gp.L; ++l) {
+        for (int l = lq; l < gp.L; l += TS / TM) {
           const int N = gp.res[l];
           const bool dense = gp.dense[l] != 0;
           int ci[3];
@@ -418,6 +440,24 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
     const int64_t idx = ts + r;
     const bool valid = idx < slot_end && idx < r1;
     uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);  // [hi | lo] of the tile
+    // this tile's stored activations: written by a training forward, read back by the backward
+    uint8_t *gact = a.acts ? reinterpret_cast<uint8_t *>(a.acts) + (ts / TM) * (int64_t)ACT : nullptr;
+    if (SV && t == 0) {
+      // the buffers' last readers (MMAs, mask loads) finished before the barrier that ended the
+      // previous tile
+      tc::fence_async_smem();
+      const uint32_t bytes = (Q8 ? 0u : (uint32_t)(TM * INP * 2)) + (uint32_t)ACT;
+      tc::mbar_arrive_expect_tx(abar, bytes);
+      if (!Q8) tc::bulk_g2s(sm + Y::X0, ftile, TM * INP * 2, abar);
+      tc::bulk_g2s(sm + Y::X1, gact + Y::A1, TM * 64 * 2, abar);
+      tc::bulk_g2s(sm + Y::X2, gact + Y::A2, TM * 64 * 2, abar);
+      if (COL) {
+        tc::bulk_g2s(sm + Y::X3, gact + Y::A3, TM * CIN * 2, abar);
+        tc::bulk_g2s(sm + Y::X4, gact + Y::A4, TM * 64 * 2, abar);
+        tc::bulk_g2s(sm + Y::X5, gact + Y::A5, TM * 64 * 2, abar);
+      }
+      a_pending = true;
+    }
 
     // ---- features ----
     const float s1 = Q8 ? e4m3_scale(a.amax[slot]) : 1.0f;  // E4M3 first layer: the slot's scale
@@ -539,13 +579,34 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
         reinterpret_cast<uint4 *>(ftile)[i] = reinterpret_cast<const uint4 *>(sm + Y::X0)[i];
         reinterpret_cast<uint4 *>(ftile + TM * INP)[i] = reinterpret_cast<const uint4 *>(sm + Y::XL0)[i];
       }
-    } else {
+    } else if (!SV) {
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
         reinterpret_cast<uint4 *>(sm + Y::X0)[i] = reinterpret_cast<const uint4 *>(ftile)[i];
         reinterpret_cast<uint4 *>(sm + Y::XL0)[i] = reinterpret_cast<const uint4 *>(ftile + TM * INP)[i];
       }
     }
     handoff();
+    float g[16];
+    float rgb[3] = {0.f, 0.f, 0.f};
+    float e0 = 0.f;  // exp(clamp(g_0, -15, 15)): the truncated-exponential gradient factor of sigma
+    if constexpr (SV) {
+      // wait for the stored activations; sigma and rgb come from the forward's output
+      const bool ok = tc::mbar_wait(abar, aphase);
+      if (ok) {
+        aphase ^= 1u;
+        if (t == 0) a_pending = false;
+      }
+      abort = tc::bar_or(kChainBar, TT, !ok);
+      if (abort) break;
+      if (ch == 0) {
+        float4 sr = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) sr = reinterpret_cast<const float4 *>(a.sigma_rgb)[idx];
+        e0 = fminf(fmaxf(sr.x, __expf(-15.f)), __expf(15.f));
+        rgb[0] = sr.y;
+        rgb[1] = sr.z;
+        rgb[2] = sr.w;
+      }
+    } else {
 
     // ---- forward MLP ----
     if (t == 0) {
@@ -556,9 +617,9 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
     abort = !sync_mma();
     if (abort) break;
     if (Q8)
-      epi64<0, false>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch, s1);
+      epi64<0, false>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch, s1, gact ? gact + Y::A1 : nullptr);
     else
-      epi64<0>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch);
+      epi64<0>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch, 1.0f, gact ? gact + Y::A1 : nullptr);
     handoff();
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X1, s0 + Y::W2, 64, 64);
@@ -567,7 +628,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
     }
     abort = !sync_mma();
     if (abort) break;
-    epi64<0>(trow, trow + Y::C_DL, sm + Y::X2, sm + Y::XLB, nullptr, r, ch);
+    epi64<0>(trow, trow + Y::C_DL, sm + Y::X2, sm + Y::XLB, nullptr, r, ch, 1.0f, gact ? gact + Y::A2 : nullptr);
     handoff();
     if (t == 0) {
       mma_fwd(tmem, s0 + Y::X2, s0 + Y::W3, 64, 16);
@@ -576,11 +637,9 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
     }
     abort = !sync_mma();
     if (abort) break;
-    float g[16];
-    float rgb[3] = {0.f, 0.f, 0.f};
     if (ch == 0) {
       ld16_pair(trow, trow + Y::C_DL, g);
-      store16(sm + Y::X3, sm + Y::XL3, r, g);
+      store16(sm + Y::X3, sm + Y::XL3, r, g, (COL && gact) ? gact + Y::A3 : nullptr);
       if (!COL) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) rgb[k] = sigm(g[1 + k]);
@@ -594,7 +653,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
         for (int q = 0; q < 3; ++q) dir[q] = a.ray_od[(int64_t)(3 + q) * a.n_rays + ray];
       }
       sh16(dir[0], dir[1], dir[2], y);
-      store16(sm + Y::X3 + TM * 16 * 2, sm + Y::XL3 + TM * 16 * 2, r, y);
+      store16(sm + Y::X3 + TM * 16 * 2, sm + Y::XL3 + TM * 16 * 2, r, y, gact ? gact + Y::A3 + TM * 16 * 2 : nullptr);
     }
     handoff();
     if (COL) {
@@ -605,7 +664,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
       }
       abort = !sync_mma();
       if (abort) break;
-      epi64<0>(trow, trow + Y::C_DL, sm + Y::X4, sm + Y::XLA, nullptr, r, ch);
+      epi64<0>(trow, trow + Y::C_DL, sm + Y::X4, sm + Y::XLA, nullptr, r, ch, 1.0f, gact ? gact + Y::A4 : nullptr);
       handoff();
       if (t == 0) {
         mma_fwd(tmem, s0 + Y::X4, s0 + Y::V2, 64, 64);
@@ -614,7 +673,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
       }
       abort = !sync_mma();
       if (abort) break;
-      epi64<0>(trow, trow + Y::C_DL, sm + Y::X5, sm + Y::XLB, nullptr, r, ch);
+      epi64<0>(trow, trow + Y::C_DL, sm + Y::X5, sm + Y::XLB, nullptr, r, ch, 1.0f, gact ? gact + Y::A5 : nullptr);
       handoff();
       if (t == 0) {
         mma_fwd(tmem, s0 + Y::X5, s0 + Y::V3, 64, 16);
@@ -633,8 +692,10 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
       tc::bar_sync(kChainBar, TT);
       tc::fence_after_sync();
     }
+    if (ch == 0) e0 = __expf(fminf(fmaxf(g[0], -15.f), 15.f));
+    }  // forward MLP (recomputed in a backward without stored activations)
 
-    if (!BWD) {
+    if constexpr (!BWD) {
       if (ch == 0 && valid)
         reinterpret_cast<float4 *>(a.sigma_rgb)[idx] = make_float4(__expf(g[0]), rgb[0], rgb[1], rgb[2]);
       continue;
@@ -645,7 +706,7 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
     if (ch == 0) {
       float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) d = reinterpret_cast<const float4 *>(a.dsr)[idx];
-      const float dg0 = d.x * __expf(fminf(fmaxf(g[0], -15.f), 15.f));
+      const float dg0 = d.x * e0;
       const float d3[3] = {d.y * rgb[0] * (1.f - rgb[0]), d.z * rgb[1] * (1.f - rgb[1]), d.w * rgb[2] * (1.f - rgb[2])};
       float row[16];
 #pragma unroll
@@ -778,6 +839,8 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
     if (t == 0) atomicOr(&st_rw->status, kStatusTimeout);
     *abort_flag = 1;             // releases scatter warps waiting for a tile
     tc::mbar_wait(mbar, phase);  // bounded: let any MMA still in flight finish before freeing TMEM
+    // bounded: bulk copies still writing this CTA's shared memory land before it exits
+    if (SV && a_pending) tc::mbar_wait(abar, aphase);
   } else if (BWD && cur_slot >= 0) {
     flush(cur_slot);
   }
@@ -788,14 +851,16 @@ __global__ void __launch_bounds__(BWD ? TT + TS : TT, MINB) k_field_tc(const Fie
   if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
 }
 
-template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB>
+template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB, bool SV = false>
 cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_ctas) {
   using Y = L<IN, BWD, VD>;
   static_assert(Y::SMEM <= 232448, "shared memory per CTA");
   static_assert(MINB * (Y::SMEM + 1024) <= 233472, "resident CTAs per SM: shared memory");
   static_assert(MINB * Y::TCOLS <= 512, "resident CTAs per SM: tensor memory");
   static_assert(Y::C_V1 + Y::CIN <= Y::C_DL || !BWD, "tensor-memory columns of dV1");
-  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL, VD, MINB>;
+  static_assert(Y::MISC % 8 == 0 && 96 <= Y::SMEM - Y::MISC, "mbarriers and tile info in the MISC block");
+  static_assert(Y::X0 % 16 == 0 && Y::X1 % 16 == 0 && Y::X3 % 16 == 0 && Y::X5 % 16 == 0, "bulk-copy targets");
+  auto k = k_field_tc<IN, G, COL, BWD, Q8, KL, VD, MINB, SV>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
@@ -807,14 +872,18 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_
   int64_t grid = (int64_t)sm_count * per_sm;
   if (grid > max_tiles) grid = max_tiles;
   if (grid <= 0) return cudaSuccess;
-  k<<<(unsigned)grid, BWD ? TT + TS : TT, Y::SMEM, st>>>(a);
+  k<<<(unsigned)grid, BWD ? TT + scatter_threads(SV) : TT, Y::SMEM, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int IN, int G, bool COL, bool Q8, bool VD>
 cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
-  if (a.mode == kBackward) return launch_t<IN, G, COL, true, Q8, 1, VD, 1>(a, sm_count, st, 1);
+  if (a.mode == kBackward) {
+    // stored activations (a training forward wrote them) or the forward recomputed
+    if (a.acts) return launch_t<IN, G, COL, true, Q8, 1, VD, 1, true>(a, sm_count, st, 1);
+    return launch_t<IN, G, COL, true, Q8, 1, VD, 1, false>(a, sm_count, st, 1);
+  }
   // three CTAs per SM: compiled for 85 registers a thread, one level of corner loads at a time
   if (tu.tc_fwd_ctas == 3) return launch_t<IN, G, COL, false, Q8, 1, VD, 3>(a, sm_count, st, 3);
   // the E4M3 forward reads its features instead of gathering them: no gather shape to pick
@@ -842,6 +911,10 @@ cudaError_t launch_in(const FieldArgs &a, int sm_count, cudaStream_t st, const T
 }
 
 }  // namespace
+
+int64_t act_tile_bytes(bool colour, bool view_dirs) {
+  return view_dirs ? L<32, true, true>::act_bytes(colour) : L<32, true, false>::act_bytes(colour);
+}
 
 cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu) {
   if (a.mode == kEncodeOnly || a.feat_lp == nullptr || a.params_lp == nullptr) return cudaErrorInvalidValue;

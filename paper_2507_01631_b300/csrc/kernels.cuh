@@ -8,6 +8,7 @@ namespace snk {
 struct Tuning {
   int tc_fwd_ctas = 3;          // tensor-core forward: persistent CTAs per SM (1, 2, 3)
   int tc_fwd_levels = 1;        // tensor-core forward: levels whose corner loads are issued together (1, 2)
+  int tc_bwd_saved = 1;         // tensor-core training step: the forward stores activations for the backward (0, 1)
   int fp32_ctas = 2;            // binary32 field kernels: persistent CTAs per SM (1, 2)
   int composite_threads = 256;  // compositing: threads per block (64 .. 512, multiple of 32)
   int sampler_threads = 256;    // ray and sample kernels: threads per block (128 .. 512, multiple of 32)
@@ -68,6 +69,7 @@ struct FieldArgs {
   float *feat32;              // E4M3 path: [S][IN] binary32 features (gather writes, forward reads)
   uint8_t *codes;             // E4M3 path: [S][IN] first-layer codes (forward writes, backward reads)
   uint32_t *amax;             // E4M3 path: per slot, bits of max |feature| of the step (>= 0 floats)
+  uint16_t *acts;             // tensor-core training step: stored activations, act_tile_bytes a tile, or null
   const uint32_t *smp_ray;    // view-direction models: [S] ray of each sample
   const float *ray_od;        // view-direction models: [6][n_rays] ray origins and directions
   int32_t n_rays;
@@ -78,6 +80,8 @@ struct FieldArgs {
 };
 cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu = Tuning());
 cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu = Tuning());
+// Bytes of one 128-sample tile of stored activations (FieldArgs::acts).
+int64_t act_tile_bytes(bool colour, bool view_dirs);
 // Scatter-add feat_in (read as dfeat [S][L*F]) into the table gradients.
 cudaError_t launch_encode_scatter(const FieldArgs &a, cudaStream_t st);
 // E4M3 path, first pass: binary32 features from the FP16 tables into feat32 and

@@ -68,7 +68,7 @@ class SnkState(Structure):
 class SnkTuning(Structure):
     _fields_ = [("tc_fwd_ctas", c_int32), ("tc_fwd_levels", c_int32), ("fp32_ctas", c_int32),
                 ("composite_threads", c_int32), ("sampler_threads", c_int32), ("tuned", c_int32),
-                ("reserved", c_int32 * 2)]
+                ("tc_bwd_saved", c_int32), ("reserved", c_int32)]
 
 
 STRUCTS = [SnkCamera, SnkWindow, SnkModel, SnkLayout, SnkSampler, SnkAdam, SnkParams, SnkState, SnkTuning]
@@ -83,6 +83,7 @@ SIGNATURES = {
     "snk_ctx_create": (c_int, [c_int, POINTER(c_void_p)]),
     "snk_ctx_destroy": (c_int, [_P]),
     "snk_ctx_reserve": (c_int, [_P, c_int64, c_int64]),
+    "snk_max_samples": (c_int64, [POINTER(SnkWindow), POINTER(SnkSampler), c_int64]),
     "snk_last_error": (c_char_p, [_P]),
     "snk_set_views": (c_int, [_P, POINTER(SnkCamera), c_int, POINTER(c_void_p), _P]),
     "snk_sample_segments": (c_int, [_P, POINTER(SnkWindow), _P, c_int, POINTER(SnkSampler), _P, _P, _P, _P, _P,
@@ -250,6 +251,10 @@ class Context:
 
     def reserve(self, max_rays, max_samples):
         self.call("snk_ctx_reserve", max_rays, max_samples)
+
+    def max_samples(self, window, sampler, n_rays):
+        """The sample capacity a step of n_rays rays sizes its workspace for (snk_max_samples)."""
+        return int(self.lib.snk_max_samples(ctypes.byref(window), ctypes.byref(sampler), int(n_rays)))
 
     def set_views(self, cams, crops=None, stream=None):
         arr = (SnkCamera * len(cams))(*[camera_struct(c) for c in cams])

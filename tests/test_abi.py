@@ -85,6 +85,28 @@ def test_view_direction_models(lib):
         assert rc == (snk.SNK_OK if ok else snk.SNK_ERR_INVALID_ARG), (prec, flag)
 
 
+def test_sample_capacity_bound(lib):
+    """snk_max_samples: a ray's segments take clamp(rint(K_ray f_s), K_min, K_max) samples with
+    the shares f_s summing to 1, so a brute-force maximum over share splits stays below the bound."""
+    from synth import workloads as W
+    rng = np.random.default_rng(0)
+    for name in ["window2x2_full", "window2x2_fp8", "tiny_window", "tile512_full"]:
+        w = W.get(name)
+        win = snk.window_struct(w.window())
+        sp = snk.sampler_struct(w.K_ray, w.K_min, w.K_max)
+        bound = lib.snk_max_samples(ctypes.byref(win), ctypes.byref(sp), 1000)
+        segs = 1 + (w.nx == 2) + (w.ny == 2)
+        f = rng.dirichlet(np.full(segs, 0.3), 20000)
+        f = np.concatenate([f, np.eye(segs), np.full((1, segs), 1.0 / segs)])
+        k = np.clip(np.rint(w.K_ray * f.astype(np.float32)), w.K_min, w.K_max).sum(1)
+        assert 1000 * k.max() <= bound - 4 * 128, (name, k.max(), bound)
+        assert bound <= 1000 * segs * w.K_max + 4 * 128
+    win = snk.window_struct(W.get("window2x2_full").window())
+    uni = snk.sampler_struct(96, 64, 128, mode=snk.SNK_SAMPLE_UNIFORM)
+    assert lib.snk_max_samples(ctypes.byref(win), ctypes.byref(uni), 10) == 10 * 96 + 4 * 128
+    assert lib.snk_max_samples(None, ctypes.byref(uni), 10) == -1
+
+
 def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.snk_model_layout(None, None) == snk.SNK_ERR_INVALID_ARG
     assert lib.snk_ctx_reserve(None, 1, 1) == snk.SNK_ERR_INVALID_ARG

@@ -1,6 +1,8 @@
 """Launch shapes (snk_autotune / snk_set_tuning): every shape computes the same
 step -- rendered outputs bit-identical, gradients equal up to the order of
-float atomics -- and the autotuner leaves the caller's training state alone."""
+float atomics; this includes the backward reading the forward's stored
+activations against recomputing them -- and the autotuner leaves the caller's
+training state alone."""
 import numpy as np
 import pytest
 
@@ -11,8 +13,9 @@ from paper_2507_01631_b300.trainer import Trainer, model_from_workload
 from gpu_util import make_case, normwise
 
 pytestmark = pytest.mark.gpu
-DEFAULT = dict(tc_fwd_ctas=2, tc_fwd_levels=1, fp32_ctas=2, composite_threads=256, sampler_threads=256)
-ALTERNATIVES = [("tc_fwd_ctas", 1), ("tc_fwd_ctas", 3), ("tc_fwd_levels", 2), ("fp32_ctas", 1), ("composite_threads", 64),
+DEFAULT = dict(tc_fwd_ctas=2, tc_fwd_levels=1, tc_bwd_saved=1, fp32_ctas=2, composite_threads=256,
+               sampler_threads=256)
+ALTERNATIVES = [("tc_fwd_ctas", 1), ("tc_fwd_ctas", 3), ("tc_fwd_levels", 2), ("tc_bwd_saved", 0), ("fp32_ctas", 1), ("composite_threads", 64),
                 ("composite_threads", 512), ("sampler_threads", 128), ("sampler_threads", 512)]
 
 
@@ -80,7 +83,7 @@ def test_autotune_picks_valid_shapes_and_leaves_the_training_state(ctx, precisio
 
 
 def test_out_of_range_tuning_is_rejected(ctx):
-    for key, val in [("tc_fwd_ctas", 4), ("tc_fwd_levels", 4), ("composite_threads", 96 + 1),
+    for key, val in [("tc_fwd_ctas", 4), ("tc_fwd_levels", 4), ("tc_bwd_saved", 2), ("composite_threads", 96 + 1),
                      ("sampler_threads", 1024), ("fp32_ctas", 0)]:
         with pytest.raises(RuntimeError):
             ctx.set_tuning(**dict(DEFAULT, **{key: val}))
