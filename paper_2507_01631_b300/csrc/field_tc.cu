@@ -168,7 +168,8 @@ __device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, 
 // [128 x 64] activation buffer).  v is written as hi (out) and scaled lo (out_lo).
 // LO = false: the layer had no low-part MMA (E4M3 first layer, whose input is exact in
 // FP16); scale multiplies the sum (the E4M3 input's per-slot scale, else 1).
-// gout (nullable): a global copy of the high parts in the same layout (stored activations).
+// gout (nullable): a global copy of the high parts in the same layout (stored activations),
+// written with the streaming (evict-first) hint so that it does not push the hash tables out of L2.
 template <int MODE, bool LO = true>
 __device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t *out, uint8_t *out_lo,
                                       const uint8_t *mask, int r, int ch, float scale = 1.0f,
@@ -214,7 +215,7 @@ __device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t
     }
     *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
     *reinterpret_cast<uint4 *>(out_lo + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
-    if (gout) *reinterpret_cast<uint4 *>(gout + off) = make_uint4(o[0], o[1], o[2], o[3]);
+    if (gout) __stcs(reinterpret_cast<uint4 *>(gout + off), make_uint4(o[0], o[1], o[2], o[3]));
   }
 }
 
@@ -243,7 +244,7 @@ __device__ __forceinline__ void store16(uint8_t *buf, uint8_t *buf_lo, int r, co
     }
     *reinterpret_cast<uint4 *>(buf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
     if (buf_lo) *reinterpret_cast<uint4 *>(buf_lo + tc::core_off(r, q * 8, TM)) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
-    if (gbuf) *reinterpret_cast<uint4 *>(gbuf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
+    if (gbuf) __stcs(reinterpret_cast<uint4 *>(gbuf + tc::core_off(r, q * 8, TM)), make_uint4(o[0], o[1], o[2], o[3]));
   }
 }
 
@@ -576,8 +577,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       tc::bar_sync(kChainBar, TT);
       // the tile's features (high and low parts), in the shared-memory layout, for the backward
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
-        reinterpret_cast<uint4 *>(ftile)[i] = reinterpret_cast<const uint4 *>(sm + Y::X0)[i];
-        reinterpret_cast<uint4 *>(ftile + TM * INP)[i] = reinterpret_cast<const uint4 *>(sm + Y::XL0)[i];
+        __stcs(reinterpret_cast<uint4 *>(ftile) + i, reinterpret_cast<const uint4 *>(sm + Y::X0)[i]);
+        __stcs(reinterpret_cast<uint4 *>(ftile + TM * INP) + i, reinterpret_cast<const uint4 *>(sm + Y::XL0)[i]);
       }
     } else if (!SV) {
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
