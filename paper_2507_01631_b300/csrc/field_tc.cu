@@ -448,14 +448,16 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       // previous tile
       tc::fence_async_smem();
       const uint32_t bytes = (Q8 ? 0u : (uint32_t)(TM * INP * 2)) + (uint32_t)ACT;
+      // read once: evict first, so that the stream leaves the slot's gradient table in L2
+      const uint64_t pol = tc::l2_evict_first();
       tc::mbar_arrive_expect_tx(abar, bytes);
-      if (!Q8) tc::bulk_g2s(sm + Y::X0, ftile, TM * INP * 2, abar);
-      tc::bulk_g2s(sm + Y::X1, gact + Y::A1, TM * 64 * 2, abar);
-      tc::bulk_g2s(sm + Y::X2, gact + Y::A2, TM * 64 * 2, abar);
+      if (!Q8) tc::bulk_g2s(sm + Y::X0, ftile, TM * INP * 2, abar, pol);
+      tc::bulk_g2s(sm + Y::X1, gact + Y::A1, TM * 64 * 2, abar, pol);
+      tc::bulk_g2s(sm + Y::X2, gact + Y::A2, TM * 64 * 2, abar, pol);
       if (COL) {
-        tc::bulk_g2s(sm + Y::X3, gact + Y::A3, TM * CIN * 2, abar);
-        tc::bulk_g2s(sm + Y::X4, gact + Y::A4, TM * 64 * 2, abar);
-        tc::bulk_g2s(sm + Y::X5, gact + Y::A5, TM * 64 * 2, abar);
+        tc::bulk_g2s(sm + Y::X3, gact + Y::A3, TM * CIN * 2, abar, pol);
+        tc::bulk_g2s(sm + Y::X4, gact + Y::A4, TM * 64 * 2, abar, pol);
+        tc::bulk_g2s(sm + Y::X5, gact + Y::A5, TM * 64 * 2, abar, pol);
       }
       a_pending = true;
     }
