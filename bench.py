@@ -80,37 +80,54 @@ def mlp_flops_per_sample(w):
     return 2 * mac
 
 
-def field_backward_work(w, precision):
+def act_bytes_per_sample(w):
+    """FP16 high parts of the activations a training forward stores for its
+    backward: h1, h2 (64 each) and, with a colour net, g (16, 32 with view
+    directions), c1, c2 (64 each)."""
+    cin = w.geo_out + (16 if w.view_dirs else 0)
+    return 2 * (128 + ((cin + 128) if w.colour else 0))
+
+
+def field_backward_work(w, precision, saved=False):
     """Algorithmic FLOPs and HBM bytes per sample of the fused field backward.
-    FLOPs: recomputed MLP forward + input gradients + weight gradients (3 x the
-    forward MACs x 2).  HBM bytes: the binary32 path re-gathers the 8 corners of
-    L levels x F binary32 table entries (the tables and their gradients are
-    L2-resident, so the gather is counted once as a stream here only for the
-    binary32 baseline); the mixed path reads back its stored features (split
-    FP16, 4 B x L*F; the E4M3 path its 1-byte codes); all read xyz (12 B) and
-    the upstream gradient (16 B).
+    FLOPs: the recomputed MLP forward (unless the forward stored its activations,
+    `saved`) + input gradients + weight gradients (3 or 2 x the forward MACs x 2).
+    HBM bytes: the binary32 path re-gathers the 8 corners of L levels x F
+    binary32 table entries (the tables and their gradients are L2-resident, so
+    the gather is counted once as a stream here only for the binary32 baseline);
+    the mixed path reads back its stored features (split FP16, 4 B x L*F; the
+    E4M3 path its 1-byte codes), or with stored activations their high parts
+    (2 B x L*F) and the activations, plus (sigma, rgb) (16 B); all read xyz
+    (12 B) and the upstream gradient (16 B).
     The scatter-add of the table gradient (8 corners x L x F binary32 RMW) goes
     to L2-resident memory and is reported as l2_red_bytes, not as HBM bytes.
     With view directions the first colour layer's input gradient covers the g
     columns only (the direction encoding has no parameters behind it), and each
     sample reads its ray index (4 B; the directions themselves are per ray)."""
-    fl = 3 * mlp_flops_per_sample(w) - (2 * 16 * 64 if w.view_dirs else 0)
+    saved = saved and precision != "fp32"
+    fl = (2 if saved else 3) * mlp_flops_per_sample(w) - (2 * 16 * 64 if w.view_dirs else 0)
     vd = 4 if w.view_dirs else 0
     if precision == "fp32":
         feat = w.L * 8 * w.F * 4
     elif precision == "mixed_e4m3":
         feat = max(16, w.L * w.F)       # the E4M3 codes, 1 B per feature
+    elif saved:
+        feat = 2 * max(16, w.L * w.F)   # high parts only
     else:
         feat = 4 * max(16, w.L * w.F)
+    if saved:
+        feat += act_bytes_per_sample(w) + 16
     return fl, feat + 12 + 16 + vd
 
 
-def field_forward_work(w, precision):
+def field_forward_work(w, precision, saved=False):
     """FLOPs: the MLP forward.  HBM bytes: xyz in (12 B), (sigma, rgb) out
     (16 B) and, on the mixed path, the split-FP16 features written for the
-    backward (4 B x L*F); the table gather (8 corners x L x F) hits the
-    L2-resident tables and is reported as l2_gather_bytes."""
+    backward (4 B x L*F) and, with `saved`, the stored activations; the table
+    gather (8 corners x L x F) hits the L2-resident tables and is reported as
+    l2_gather_bytes."""
     vd = 4 if w.view_dirs else 0  # the sample's ray index (view-direction colour input)
+    vd += act_bytes_per_sample(w) if (saved and precision != "fp32") else 0
     if precision == "fp32":
         return mlp_flops_per_sample(w), 12 + 16 + vd
     if precision == "mixed_e4m3":
@@ -121,9 +138,10 @@ def field_forward_work(w, precision):
 
 
 # DRAM bytes per sample of each kernel measured by ncu (--set full) on the 32768-ray case of the
-# 512 m tile (tile-local traffic grows with the samples processed); null once a kernel changes.
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward"): 174.2, ("mixed", "field_forward"): 149.2,
-                            ("fp32", "field_backward"): 736.6, ("fp32", "field_forward"): 42.5}
+# 512 m tile (tile-local traffic grows with the samples processed), keyed by (precision, kernel,
+# stored activations); a kernel changed since its capture has no entry (traffic null).
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True): 676.5, ("mixed", "field_forward", True): 690.6,
+                            ("fp32", "field_backward", False): 736.6, ("fp32", "field_forward", False): 42.5}
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -483,14 +501,15 @@ def run_ours(args, w):
         name, (sms, calls) = max(stages.items(), key=lambda kv: kv[1][0])
         per_launch_s = (sms / max(calls, 1)) / 1000.0
         per_step_samples = n_samples / max(args.steps, 1)
+        saved = bool(tuning.get("tc_bwd_saved", 0)) and prec_key != "fp32"
         if name == "field_backward":
-            fl, by = field_backward_work(w, prec_key)
+            fl, by = field_backward_work(w, prec_key, saved)
         elif name == "field_forward":
-            fl, by = field_forward_work(w, prec_key)
+            fl, by = field_forward_work(w, prec_key, saved)
         else:
             fl, by = 0, 0
         sm_max = pk.get("sm_max_mhz", 2032.0)
-        dram = MEASURED_DRAM_PER_SAMPLE.get((prec_key, name))
+        dram = MEASURED_DRAM_PER_SAMPLE.get((prec_key, name, saved))
         traffic = dram * per_step_samples if dram is not None else None
         l2 = {"l2_gather_bytes_per_sample": w.L * 8 * w.F * (4 if args.precision == "fp32" else 2),
               "l2_red_bytes_per_sample": w.L * 8 * w.F * 4 * 2 if name == "field_backward" else 0}
