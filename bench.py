@@ -127,7 +127,8 @@ def field_forward_work(w, precision, saved=False):
     gather (8 corners x L x F) hits the L2-resident tables and is reported as
     l2_gather_bytes."""
     vd = 4 if w.view_dirs else 0  # the sample's ray index (view-direction colour input)
-    vd += act_bytes_per_sample(w) if (saved and precision != "fp32") else 0
+    if saved and precision == "mixed":
+        vd += act_bytes_per_sample(w) - 2 * max(16, w.L * w.F)  # activations stored; feature low parts not
     if precision == "fp32":
         return mlp_flops_per_sample(w), 12 + 16 + vd
     if precision == "mixed_e4m3":
@@ -140,7 +141,7 @@ def field_forward_work(w, precision, saved=False):
 # DRAM bytes per sample of each kernel measured by ncu (--set full) on the 32768-ray case of the
 # 512 m tile (tile-local traffic grows with the samples processed), keyed by (precision, kernel,
 # stored activations); a kernel changed since its capture has no entry (traffic null).
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True): 676.5, ("mixed", "field_forward", True): 690.6,
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True): 676.5,
                             ("fp32", "field_backward", False): 736.6, ("fp32", "field_forward", False): 42.5}
 
 

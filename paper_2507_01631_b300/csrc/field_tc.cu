@@ -577,10 +577,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
         }
       }
       tc::bar_sync(kChainBar, TT);
-      // the tile's features (high and low parts), in the shared-memory layout, for the backward
+      // the tile's features in the shared-memory layout, for the backward: the high parts, and
+      // the low parts unless the activations are stored (the backward then needs the high parts
+      // only, for dW1)
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
         __stcs(reinterpret_cast<uint4 *>(ftile) + i, reinterpret_cast<const uint4 *>(sm + Y::X0)[i]);
-        __stcs(reinterpret_cast<uint4 *>(ftile + TM * INP) + i, reinterpret_cast<const uint4 *>(sm + Y::XL0)[i]);
+        if (!gact) __stcs(reinterpret_cast<uint4 *>(ftile + TM * INP) + i, reinterpret_cast<const uint4 *>(sm + Y::XL0)[i]);
       }
     } else if (!SV) {
       for (int i = t; i < TM * INP * 2 / 16; i += TT) {
