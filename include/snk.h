@@ -477,6 +477,14 @@ int snk_stage_times(snk_ctx *ctx, double *ms, int64_t *calls, int n);
  * status code (SNK_ERR_DEVICE_CHECK, SNK_ERR_TIMEOUT, SNK_ERR_OVERFLOW). */
 int snk_sync_status(snk_ctx *ctx, const snk_state *state, snk_stream_t stream);
 
+/* Self-test of the bounded device waits (every mbarrier wait of the tensor-core
+ * field kernels gives up after 2 s, sets the timeout bit of the step state and
+ * returns): one CTA waits on an mbarrier that receives its arrival (arrive != 0:
+ * the wait completes, state unchanged) or never does (arrive == 0: after 2 s the
+ * timeout bit is set, so snk_sync_status returns SNK_ERR_TIMEOUT, and the context
+ * stays usable).  state: device snk_state (not cleared here).  Asynchronous. */
+int snk_wait_selftest(snk_ctx *ctx, int arrive, snk_state *state, snk_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1120,6 +1120,13 @@ int snk_quantize_e4m3(snk_ctx *ctx, const float *x, int64_t n, float scale, uint
 
 int64_t snk_launch_count(void) { return snk::g_launches.load(); }
 
+int snk_wait_selftest(snk_ctx *ctx, int arrive, snk_state *state, snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (!state) return fail(ctx, SNK_ERR_INVALID_ARG, "snk_wait_selftest: state is NULL");
+  SNK_CK(ctx, launch_wait_selftest(arrive, state, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
 int snk_stage_timing(snk_ctx *ctx, int enable) {
   if (!ctx) return SNK_ERR_INVALID_ARG;
   SNK_CK(ctx, cudaDeviceSynchronize());

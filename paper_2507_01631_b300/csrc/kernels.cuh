@@ -80,6 +80,8 @@ struct FieldArgs {
 };
 cudaError_t launch_field_fp32(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu = Tuning());
 cudaError_t launch_field_tc(const FieldArgs &a, int sm_count, cudaStream_t st, const Tuning &tu = Tuning());
+// One CTA in a bounded mbarrier wait that completes (arrive != 0) or gives up (timeout bit).
+cudaError_t launch_wait_selftest(int arrive, snk_state *state, cudaStream_t st);
 // Bytes of one 128-sample tile of stored activations (FieldArgs::acts).
 int64_t act_tile_bytes(bool colour, bool view_dirs);
 // Scatter-add feat_in (read as dfeat [S][L*F]) into the table gradients.

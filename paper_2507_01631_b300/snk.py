@@ -116,6 +116,7 @@ SIGNATURES = {
                                            POINTER(SnkSampler), _P, _P, _P, _P, _P, _P, _P, _P, _P, c_int64, _P, _P,
                                            c_char_p, c_int]),
     "snk_launch_count": (c_int64, []),
+    "snk_wait_selftest": (c_int, [_P, c_int, _P, _P]),
     "snk_stage_timing": (c_int, [_P, c_int]),
     "snk_stage_times": (c_int, [_P, POINTER(c_double), POINTER(c_int64), c_int]),
 }

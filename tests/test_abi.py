@@ -112,3 +112,4 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.snk_ctx_reserve(None, 1, 1) == snk.SNK_ERR_INVALID_ARG
     assert lib.snk_ctx_destroy(None) == snk.SNK_OK
     assert lib.snk_sync_status(None, None, None) == snk.SNK_ERR_INVALID_ARG
+    assert lib.snk_wait_selftest(None, 0, None, None) == snk.SNK_ERR_INVALID_ARG
