@@ -311,7 +311,12 @@ int snk_composite_backward(snk_ctx *ctx, const float *sigma_rgb, const float *sm
  * state->iteration += 1.  SNK_MIXED adds dynamic loss scaling: a step with
  * non-finite gradients is skipped (status bit 0) and the scale halved.
  * Optional outputs (nullable): out [B][5] rendered (r, g, b, depth, opacity).
- * Never synchronises; read state (device) for loss and counts. */
+ * Never synchronises; read state (device) for loss and counts -- except when the
+ * context's workspace must grow: the batch needs snk_max_samples(win, sampler, B)
+ * samples of capacity and, on the tensor-core path with tc_bwd_saved (the
+ * default), a stored-activation buffer for that capacity; the first step that
+ * needs more allocates it (synchronising), so reserve before capturing a graph
+ * and run one step eagerly.  SNK_ERR_OOM when an allocation fails. */
 int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
                    const snk_sampler *sampler, const snk_adam *adam, const snk_params *p, snk_state *state,
                    float *out, snk_stream_t stream);
