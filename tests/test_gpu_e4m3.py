@@ -163,3 +163,20 @@ def test_e4m3_training_reduces_the_loss(ctx):
         losses.append(tr.read_state()["loss"])
     assert ctx.sync_status(tr.state) == snk.SNK_OK
     assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
+
+
+def test_stored_and_recomputed_activations_agree(ctx):
+    """The backward reading the forward's stored activations and the backward
+    recomputing them compute the same step (moments up to the order of float atomics)."""
+    case = make_case("tiny_window_fp8", n_rays=160, table_scale=0.3)
+    ms = []
+    for saved in (1, 0):
+        ctx.set_tuning(tc_bwd_saved=saved)
+        tr = _trainer(ctx, case)
+        out = torch.zeros(160 * 5, dtype=torch.float32, device="cuda")
+        tr.train_step(torch.from_numpy(case.pix.view(np.int32)).cuda(), out)
+        assert ctx.sync_status(tr.state) == snk.SNK_OK
+        ms.append((out.cpu().numpy(), tr.m.cpu().numpy().astype(np.float64)))
+    ctx.set_tuning(tc_bwd_saved=1)
+    assert np.array_equal(ms[0][0], ms[1][0])
+    assert normwise(ms[0][1], ms[1][1]) < 1e-5

@@ -144,3 +144,20 @@ def test_zero_direction_weights_reduce_to_the_model_without_directions(ctx, prec
         # the same sums in the same order, except the scatter's atomic order (tables) and flushes
         assert normwise(a.astype(np.float64), b.astype(np.float64)) < 1e-6
 
+
+
+def test_stored_and_recomputed_activations_agree(ctx):
+    """Mixed path with view directions: the backward reading the stored activations
+    and the backward recomputing them compute the same step."""
+    case = make_case(NAME, n_rays=300, table_scale=0.3)
+    ms = []
+    for saved in (1, 0):
+        ctx.set_tuning(tc_bwd_saved=saved)
+        tr = _trainer(ctx, case, snk.SNK_MIXED)
+        out = torch.zeros(300 * 5, dtype=torch.float32, device="cuda")
+        tr.train_step(dev(case.pix.view(np.int32)), out)
+        assert ctx.sync_status(tr.state) == snk.SNK_OK
+        ms.append((out.cpu().numpy(), tr.m.cpu().numpy().astype(np.float64)))
+    ctx.set_tuning(tc_bwd_saved=1)
+    assert np.array_equal(ms[0][0], ms[1][0])
+    assert normwise(ms[0][1], ms[1][1]) < 1e-5
