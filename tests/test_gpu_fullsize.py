@@ -139,3 +139,24 @@ def test_stored_and_recomputed_activations_agree_at_full_size(setup):
     setup["ctx"].set_tuning(tc_bwd_saved=setup["tuning"]["tc_bwd_saved"])
     assert np.array_equal(out1, out0)
     assert normwise(tr1.m.cpu().numpy().astype(np.float64), tr0.m.cpu().numpy().astype(np.float64)) < 1e-5
+
+
+def test_binary32_per_tile_step_renders_sampled_rays_like_the_oracle(setup):
+    """The comparison arm of the headline metric: the binary32 path, one launch chain per
+    tile, on the same full batch; rendered sampled rays within the binary32 tolerance of the
+    oracle on the binary32 parameters."""
+    from gpu_util import RGB_REL_FP32
+    w = setup["w"]
+    tr = Trainer(setup["ctx"], model_from_workload(w, snk.SNK_FP32), setup["win"], setup["sp"], setup["params"])
+    B = len(setup["pix"])
+    out = torch.zeros(B * 5, dtype=torch.float32, device="cuda")
+    tr.train_step(setup["pix_t"], out)
+    assert setup["ctx"].sync_status(tr.state) == snk.SNK_OK
+    out = out.cpu().numpy().reshape(B, 5)
+    ids = np.sort(np.random.default_rng(5).choice(B, N_CHECK, replace=False))
+    ref = OS.render_rays(setup["cfg"], setup["params"].astype(np.float64), setup["cams"], w.window(),
+                         setup["pix"][ids], seed=1234, iteration=0, render_mode=False, ray_ids=ids)
+    for nm, a, b in [("rgb", out[ids, :3], ref.rgb), ("depth", out[ids, 3], ref.depth),
+                     ("opacity", out[ids, 4], ref.opacity)]:
+        ok, err = close(a, b, RGB_REL_FP32)
+        assert ok, (nm, err)
