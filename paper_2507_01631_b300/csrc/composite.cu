@@ -6,7 +6,9 @@
 // One warp per ray.  Forward: per 32-sample chunk a warp inclusive scan of
 // tau = sigma * delta gives T_i = exp(-sum_{j<i} tau_j); alpha_i = 1 -
 // exp(-tau_i) (computed as -expm1 so that thin samples keep their weight);
-// w_i = T_i alpha_i.  The weights are parked in the gradient buffer.
+// w_i = T_i alpha_i.  The weights are kept in shared memory for the backward
+// (rays of up to kParkChunks x 32 samples; longer ones park them in the
+// gradient buffer).
 // Backward (reverse chunk order, reverse warp scans): with g = dLoss/dC,
 //   dLoss/dc_i     = w_i g
 //   dLoss/dsigma_i = delta_i (T_{i+1} (g . c_i) - sum_{j>i} w_j (g . c_j)),
@@ -36,9 +38,13 @@ __device__ __forceinline__ float warp_rev_scan(float v, int lane) {
   return v;
 }
 
+constexpr int kParkChunks = 16;  // 32-sample chunks of a ray whose weights stay in shared memory
+
 __global__ void __launch_bounds__(512) k_composite(const CompositeArgs a) {
+  extern __shared__ float wpark[];  // [warps of the block][kParkChunks][32]
   const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
+  float *wp = wpark + (threadIdx.x >> 5) * kParkChunks * 32;
   if (r >= a.B) return;
   const bool none = a.state != nullptr && a.state->n_samples == 0u;
   uint32_t n[3], off[3];
@@ -49,6 +55,10 @@ __global__ void __launch_bounds__(512) k_composite(const CompositeArgs a) {
   }
   const float4 *sr = reinterpret_cast<const float4 *>(a.sigma_rgb);
   float4 *dsr = reinterpret_cast<float4 *>(a.dsr);
+  // first chunk of each segment in the ray's chunk sequence; park in shared memory if all fit
+  const int cs1 = (int)((n[0] + 31) / 32), cs2 = cs1 + (int)((n[1] + 31) / 32);
+  const bool park = cs2 + (int)((n[2] + 31) / 32) <= kParkChunks;
+  int chunk = 0;
 
   float carry = 0.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f, op = 0.f;
 #pragma unroll 1
@@ -73,7 +83,13 @@ __global__ void __launch_bounds__(512) k_composite(const CompositeArgs a) {
       cb = fmaf(w, c.w, cb);
       dep = fmaf(w, t, dep);
       op += w;
-      if (dsr != nullptr && v) dsr[q] = make_float4(w, 0.f, 0.f, 0.f);
+      if (dsr != nullptr) {
+        if (park)
+          wp[chunk * 32 + lane] = w;
+        else if (v)
+          dsr[q] = make_float4(w, 0.f, 0.f, 0.f);
+      }
+      ++chunk;
       carry += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
@@ -122,6 +138,7 @@ __global__ void __launch_bounds__(512) k_composite(const CompositeArgs a) {
   for (int s = 2; s >= 0; --s) {
     if (n[s] == 0) continue;
     const int nch = (int)((n[s] + 31) / 32);
+    const int cs = s == 0 ? 0 : (s == 1 ? cs1 : cs2);
     for (int ch = nch - 1; ch >= 0; --ch) {
       const uint32_t i = (uint32_t)ch * 32 + lane;
       const bool v = i < n[s];
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(512) k_composite(const CompositeArgs a) {
       float w = 0.f, dt = 0.f;
       float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
       if (v) {
-        w = dsr[q].x;
+        w = park ? wp[(cs + ch) * 32 + lane] : dsr[q].x;
         c = sr[q];
         dt = a.smp_dt[q];
       }
@@ -153,7 +170,7 @@ cudaError_t launch_composite(const CompositeArgs &a, cudaStream_t st, const Tuni
   if (a.B <= 0) return cudaSuccess;
   const int64_t threads = (int64_t)a.B * 32;
   const int nt = tu.composite_threads;
-  k_composite<<<(unsigned)((threads + nt - 1) / nt), nt, 0, st>>>(a);
+  k_composite<<<(unsigned)((threads + nt - 1) / nt), nt, sizeof(float) * (nt / 32) * kParkChunks * 32, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
