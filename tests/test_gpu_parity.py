@@ -310,6 +310,65 @@ def test_composite_forward_and_backward(ctx, name, n_rays):
     assert normwise(gd[:, 1:], drgb) < GRAD_REL_FP32
 
 
+def test_composite_long_rays_and_segment_edges(ctx):
+    """Synthetic segment counts around the compositing kernel's shared-memory limit for a ray's
+    weights (16 chunks of 32 samples): rays of exactly 512 samples keep them on chip, longer
+    ones (513, 700 and 900 samples) park them in the gradient buffer; also segments of one
+    sample, segments that end a chunk early, and an empty ray.  Forward and backward against
+    the oracle's compositing."""
+    counts = np.array([[512, 0, 0], [513, 0, 0], [400, 200, 100], [300, 300, 300], [31, 1, 0], [1, 1, 1],
+                       [0, 0, 0], [33, 64, 65], [0, 17, 0], [256, 0, 256]], np.int64)
+    B = len(counts)
+    rng = np.random.default_rng(11)
+    n = int(counts.sum())
+    seg_off = np.zeros((B, 3), np.int64)
+    ray_off = np.zeros(B + 1, np.int64)
+    t = np.zeros(n, np.float32)
+    dt = np.zeros(n, np.float32)
+    p = 0
+    for r in range(B):
+        ray_off[r] = p
+        tt = 0.0
+        for sgm in range(3):
+            seg_off[r, sgm] = p
+            for _ in range(counts[r, sgm]):
+                d = rng.uniform(0.01, 0.2)
+                t[p], dt[p] = tt + 0.5 * d, d
+                tt += d
+                p += 1
+    ray_off[B] = p
+    sr_h = np.zeros((n, 4), np.float32)
+    sr_h[:, 0] = rng.gamma(1.0, 0.02, n)
+    sr_h[:, 1:] = rng.uniform(0, 1, (n, 3))
+    sr, td, dtd = dev(sr_h), dev(t), dev(dt)
+    sn, so = dev(counts.astype(np.int32)), dev(seg_off.astype(np.int32))
+    out = torch.zeros(B * 5, dtype=torch.float32, device="cuda")
+    tfin = torch.zeros(B, dtype=torch.float32, device="cuda")
+    ctx.call("snk_composite", snk.ptr(sr), snk.ptr(td), snk.ptr(dtd), snk.ptr(sn), snk.ptr(so), B, snk.ptr(out),
+             snk.ptr(tfin), None)
+    g_rgb_h = rng.normal(0, 1, (B, 3)).astype(np.float32)
+    dsr = torch.zeros(n * 4, dtype=torch.float32, device="cuda")
+    ctx.call("snk_composite_backward", snk.ptr(sr), snk.ptr(td), snk.ptr(dtd), snk.ptr(sn), snk.ptr(so), B,
+             snk.ptr(dev(g_rgb_h)), snk.ptr(dsr), None)
+    torch.cuda.synchronize()
+    s64 = sr_h.astype(np.float64)
+    rgb, depth, op, tf, _ = render.composite(s64[:, 0], s64[:, 1:], t.astype(np.float64), dt.astype(np.float64),
+                                             ray_off)
+    go = out.cpu().numpy().reshape(B, 5)
+    for name_, a, b in [("rgb", go[:, :3], rgb), ("depth", go[:, 3], depth), ("opacity", go[:, 4], op),
+                        ("T_final", tfin.cpu().numpy(), tf)]:
+        ok, err = close(a, b, RGB_REL_FP32)
+        assert ok, (name_, err)
+    dsig, drgb = render.composite_backward(g_rgb_h.astype(np.float64), s64[:, 0], s64[:, 1:], t.astype(np.float64),
+                                           dt.astype(np.float64), ray_off)
+    gd = dsr.cpu().numpy().reshape(n, 4)
+    for r in range(B):  # per ray, so that a wrong chunk on one path cannot hide in the norm
+        a, b = ray_off[r], ray_off[r + 1]
+        if b > a:
+            assert normwise(gd[a:b, 0], dsig[a:b]) < GRAD_REL_FP32, r
+            assert normwise(gd[a:b, 1:], drgb[a:b]) < GRAD_REL_FP32, r
+
+
 def _trainer(ctx, case, precision=snk.SNK_FP32, seed=5):
     w = case.w
     crops = [dev(t.astype(np.float32)) for t in case.targets]
