@@ -434,8 +434,7 @@ int snk_tile_unpark(snk_ctx *ctx, const snk_model *model, const snk_params *p, i
 /* Launch shapes of the context's kernels (the paper has no counterpart: they
  * change speed, never results beyond the order of float atomics). */
 typedef struct {
-    int32_t tc_fwd_ctas;       /* tensor-core forward: persistent CTAs per SM, 1, 2 or 3 (3: one level of
-                                  corner loads at a time, tc_fwd_levels is then ignored) */
+    int32_t tc_fwd_ctas;       /* tensor-core forward: persistent CTAs per SM, 1, 2 or 3 */
     int32_t tc_fwd_levels;     /* tensor-core forward: levels whose corner loads are issued together, 1 or 2 */
     int32_t fp32_ctas;         /* binary32 field kernels: persistent CTAs per SM, 1 or 2 */
     int32_t composite_threads; /* compositing kernel: threads per block, 64..512, multiple of 32 */

@@ -945,7 +945,6 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
         for (int c : {1, 2, 3})
           for (int l : {1, 2}) {
             if (l == 2 && model->precision == SNK_MIXED_E4M3) continue;  // no gather in that forward
-            if (l == 2 && c == 3) continue;                              // three CTAs: one level at a time
             ctx->tune.tc_fwd_ctas = c;
             ctx->tune.tc_fwd_levels = l;
             const double ms = time([&] { return field(kForward); }, 2);

@@ -889,8 +889,11 @@ cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, const
     if (a.acts) return launch_t<IN, G, COL, true, Q8, 1, VD, 1, true>(a, sm_count, st, 1);
     return launch_t<IN, G, COL, true, Q8, 1, VD, 1, false>(a, sm_count, st, 1);
   }
-  // three CTAs per SM: compiled for 85 registers a thread, one level of corner loads at a time
-  if (tu.tc_fwd_ctas == 3) return launch_t<IN, G, COL, false, Q8, 1, VD, 3>(a, sm_count, st, 3);
+  // three CTAs per SM: compiled for at most 85 registers a thread
+  if (tu.tc_fwd_ctas == 3) {
+    if (!Q8 && tu.tc_fwd_levels == 2) return launch_t<IN, G, COL, false, Q8, 2, VD, 3>(a, sm_count, st, 3);
+    return launch_t<IN, G, COL, false, Q8, 1, VD, 3>(a, sm_count, st, 3);
+  }
   // the E4M3 forward reads its features instead of gathering them: no gather shape to pick
   if (!Q8 && tu.tc_fwd_levels == 2)
     return launch_t<IN, G, COL, false, Q8, 2, VD, 2>(a, sm_count, st, tu.tc_fwd_ctas);

@@ -49,8 +49,11 @@ def test_every_launch_shape_computes_the_same_step(ctx, precision):
     case = make_case("window2x2_full", n_rays=384, crop=48, table_scale=0.3)
     ctx.set_tuning(**DEFAULT)
     out0, m0, loss0 = _step(ctx, case, precision)
-    for key, val in ALTERNATIVES:
-        ctx.set_tuning(**dict(DEFAULT, **{key: val}))
+    for key, val in ALTERNATIVES + [("tc_fwd_ctas", (3, 2))]:
+        if val == (3, 2):  # three CTAs per SM with two levels of corner loads in flight
+            ctx.set_tuning(**dict(DEFAULT, tc_fwd_ctas=3, tc_fwd_levels=2))
+        else:
+            ctx.set_tuning(**dict(DEFAULT, **{key: val}))
         out, m, loss = _step(ctx, case, precision)
         assert np.array_equal(out, out0), (key, val)
         assert abs(loss - loss0) <= 1e-6 * abs(loss0), (key, val)
