@@ -13,7 +13,7 @@ paper (and the works it defers to) defines it:
                  jitter and parameter initialisation.
 * ``camera``   - localisation of a pixel with an affine or cubic rational
                  (RPC-like) camera and the ray through z_max / z_min
-                 (Sec. 3 and Sec. 4.6, "On-the-fly Ray Calculation").
+                 (Sec. 3 and Sec. 4.6: rays are computed when needed).
 * ``sampler``  - ray/box clipping, 2x2-window acceptance (Sec. 4.4) and the
                  segmented sampler (Sec. 4.5).
 * ``hashgrid`` - multiresolution hash encoding (Sec. 4.1, NGP).

@@ -1,7 +1,7 @@
 // S1 + S2: on-the-fly rays from satellite cameras, window acceptance, segment
 // split, samples per segment, slot-major sample offsets and stratified sample
-// placement.  Sec. 3 / 4.6 ("On-the-fly Ray Calculation": rays are computed
-// when needed, never stored for whole images), Sec. 4.4 (accept only rays
+// placement.  Sec. 3 / 4.6 (rays are computed when needed, never stored for
+// whole images), Sec. 4.4 (accept only rays
 // whose tiles are all loaded), Sec. 4.5 (per-tile near/far pairs; each
 // segment is sampled on its own so that its ends fall on tile faces).
 //
