@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--bwd-saved", default="auto", choices=["auto", "0", "1"],
                     help="tensor-core backward: 1 reads the activations the forward stored, 0 recomputes "
                          "the forward, auto lets the autotuner (or the default) decide")
+    ap.add_argument("--fwd-split", default="auto", choices=["auto", "0", "1"],
+                    help="tensor-core forward: 1 dedicated gather warps, 0 every thread gathers then runs "
+                         "the chain, auto lets the autotuner (or the default) decide")
     ap.add_argument("--sampler-mode", default="segments", choices=["segments", "uniform", "points"],
                     help="variant: the per-tile segmented sampler, the NeRF-XL uniform distribution, "
                          "or point samples with backward-difference deltas")
@@ -141,12 +144,16 @@ def field_forward_work(w, precision, saved=False):
     return mlp_flops_per_sample(w), 12 + 16 + 4 * max(16, w.L * w.F) + vd
 
 
-# DRAM bytes per sample of each kernel measured by ncu (--set full) on the 32768-ray case of the
-# 512 m tile (tile-local traffic grows with the samples processed), keyed by (precision, kernel,
-# stored activations); a kernel changed since its capture has no entry (traffic null).
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True): 675.6, ("mixed", "field_forward", True): 626.2,
-                            ("mixed", "field_backward", False): 173.1, ("mixed", "field_forward", False): 146.0,
-                            ("fp32", "field_backward", False): 736.6, ("fp32", "field_forward", False): 42.5}
+# DRAM bytes per sample of each kernel measured by ncu on the 32768-ray case of the 512 m tile
+# (tile-local traffic grows with the samples processed), keyed by (precision, kernel, stored
+# activations, forward shape: "split" = dedicated gather warps, "chain" = every thread gathers
+# then runs the chain); a kernel changed since its capture has no entry (traffic null).
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True, ""): 675.6, ("mixed", "field_backward", False, ""): 173.1,
+                            ("mixed", "field_forward", True, "split"): 625.9,
+                            ("mixed", "field_forward", False, "split"): 146.0,
+                            ("mixed", "field_forward", True, "chain"): 626.2,
+                            ("mixed", "field_forward", False, "chain"): 146.0,
+                            ("fp32", "field_backward", False, ""): 736.6, ("fp32", "field_forward", False, ""): 42.5}
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -410,6 +417,9 @@ def run_ours(args, w):
         # the forward shape the tuner picked for the other mode may differ; keep its choice otherwise
         ctx.set_tuning(tc_bwd_saved=int(args.bwd_saved))
         tuning = ctx.tuning()
+    if args.fwd_split != "auto":
+        ctx.set_tuning(tc_fwd_split=int(args.fwd_split))
+        tuning = ctx.tuning()
     # warm-up
     for i in range(args.warmup):
         tr.train_step(batches[i % N_BATCHES], stream=stream)
@@ -518,7 +528,10 @@ def run_ours(args, w):
         else:
             fl, by = 0, 0
         sm_max = pk.get("sm_max_mhz", 2032.0)
-        dram = MEASURED_DRAM_PER_SAMPLE.get((prec_key, name, saved))
+        shape = ""
+        if name == "field_forward" and prec_key == "mixed":
+            shape = "split" if tuning.get("tc_fwd_split", 0) else "chain"
+        dram = MEASURED_DRAM_PER_SAMPLE.get((prec_key, name, saved, shape))
         traffic = dram * per_step_samples if dram is not None else None
         l2 = {"l2_gather_bytes_per_sample": w.L * 8 * w.F * (4 if args.precision == "fp32" else 2),
               "l2_red_bytes_per_sample": w.L * 8 * w.F * 4 * 2 if name == "field_backward" else 0}

@@ -446,7 +446,11 @@ typedef struct {
                                   the reserved samples, and the backward copies them back instead of
                                   recomputing the forward; 0 the backward recomputes them.  Same results
                                   either way (up to the order of float atomics). */
-    int32_t reserved;
+    int32_t tc_fwd_split;      /* tensor-core forward: 1 (default) eight gather warps a CTA interpolate the
+                                  next tile's features while four MMA / epilogue warps run the current
+                                  tile's MLP chain, two CTAs per SM (tc_fwd_ctas unused); 0 every thread
+                                  gathers a tile's features, then runs its chain (tc_fwd_ctas CTAs per
+                                  SM).  Either with tc_fwd_levels; both unused by the E4M3 model. */
 } snk_tuning;
 
 /* Current launch shapes of ctx (defaults until tuned or set). */

@@ -814,7 +814,7 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
 static bool tuning_ok(const snk_tuning &t) {
   auto mult32 = [](int v, int lo, int hi) { return v >= lo && v <= hi && v % 32 == 0; };
   return (t.tc_fwd_ctas >= 1 && t.tc_fwd_ctas <= 3) && (t.tc_fwd_levels == 1 || t.tc_fwd_levels == 2) &&
-         (t.tc_bwd_saved == 0 || t.tc_bwd_saved == 1) &&
+         (t.tc_bwd_saved == 0 || t.tc_bwd_saved == 1) && (t.tc_fwd_split == 0 || t.tc_fwd_split == 1) &&
          (t.fp32_ctas == 1 || t.fp32_ctas == 2) && mult32(t.composite_threads, 64, 512) &&
          mult32(t.sampler_threads, 128, 512);
 }
@@ -822,6 +822,7 @@ static void to_abi(const snk::Tuning &u, bool tuned, snk_tuning *t) {
   memset(t, 0, sizeof(*t));
   t->tc_fwd_ctas = u.tc_fwd_ctas;
   t->tc_fwd_levels = u.tc_fwd_levels;
+  t->tc_fwd_split = u.tc_fwd_split;
   t->fp32_ctas = u.fp32_ctas;
   t->tc_bwd_saved = u.tc_bwd_saved;
   t->composite_threads = u.composite_threads;
@@ -840,6 +841,7 @@ int snk_set_tuning(snk_ctx *ctx, const snk_tuning *in) {
   if (!tuning_ok(*in)) return fail(ctx, SNK_ERR_INVALID_ARG, "snk_set_tuning: value out of range");
   ctx->tune.tc_fwd_ctas = in->tc_fwd_ctas;
   ctx->tune.tc_fwd_levels = in->tc_fwd_levels;
+  ctx->tune.tc_fwd_split = in->tc_fwd_split;
   ctx->tune.fp32_ctas = in->fp32_ctas;
   ctx->tune.tc_bwd_saved = in->tc_bwd_saved;
   ctx->tune.composite_threads = in->composite_threads;
@@ -941,17 +943,21 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
         if (sv == 1 && ensure_acts(ctx, model, st) != SNK_OK) continue;  // no room: recompute only
         ctx->tune.tc_bwd_saved = sv;
         best = -1.0;
-        int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels;
-        for (int c : {1, 2, 3})
-          for (int l : {1, 2}) {
-            if (l == 2 && model->precision == SNK_MIXED_E4M3) continue;  // no gather in that forward
-            ctx->tune.tc_fwd_ctas = c;
-            ctx->tune.tc_fwd_levels = l;
-            const double ms = time([&] { return field(kForward); }, 2);
-            if (ms < 0) break;
-            if (best < 0 || ms < best) best = ms, pc = c, pl = l;
-          }
+        int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels, ps = saved.tc_fwd_split;
+        // (split, CTAs per SM, levels): dedicated gather warps run two CTAs per SM
+        const int shapes[8][3] = {{1, 2, 1}, {1, 2, 2}, {0, 1, 1}, {0, 1, 2}, {0, 2, 1}, {0, 2, 2}, {0, 3, 1}, {0, 3, 2}};
+        for (const auto &sh : shapes) {
+          // no gather in the E4M3 forward: one shape
+          if (model->precision == SNK_MIXED_E4M3 && (sh[0] == 1 || sh[2] == 2)) continue;
+          ctx->tune.tc_fwd_split = sh[0];
+          ctx->tune.tc_fwd_ctas = sh[1];
+          ctx->tune.tc_fwd_levels = sh[2];
+          const double ms = time([&] { return field(kForward); }, 2);
+          if (ms < 0) break;
+          if (best < 0 || ms < best) best = ms, ps = sh[0], pc = sh[1], pl = sh[2];
+        }
         if (rc) break;
+        ctx->tune.tc_fwd_split = ps;
         ctx->tune.tc_fwd_ctas = pc;
         ctx->tune.tc_fwd_levels = pl;
         if (field(kForward) != SNK_OK) break;  // this mode's forward outputs for its backward

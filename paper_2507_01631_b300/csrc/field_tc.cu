@@ -9,7 +9,10 @@
 // epilogue (ReLU, FP16 cast) goes tensor memory -> registers -> shared memory
 // and feeds the next MMA.  The FP16 features of the tile are also written to
 // global memory (64 bytes per sample) so that the backward does not re-gather
-// 512 bytes per sample from the tables.
+// 512 bytes per sample from the tables.  Two forms: k_field_tc, whose threads
+// gather a tile and then run its chain (1-3 CTAs per SM), and k_field_fws, whose
+// eight gather warps fill one of two feature buffers while its four MMA /
+// epilogue warps run the previous tile's chain (2 CTAs per SM; the default).
 //
 // Backward (per tile, one CTA per SM): warps 0-7 reload the features and
 // either recompute the MLP activations or (a training step whose forward stored
@@ -154,9 +157,10 @@ __device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, i
 }
 
 // Copy a row-major [rows x cols] 16-bit matrix from global into the core layout (R = rpad rows,
-// C = cpad columns), zero-padding, by the TT MMA / epilogue threads.
-__device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, int rows, int cols, int rpad, int cpad) {
-  for (int e = threadIdx.x; e < rpad * cpad; e += TT) {
+// C = cpad columns), zero-padding, by the first nthreads threads (the MMA / epilogue threads).
+__device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, int rows, int cols, int rpad, int cpad,
+                                             int nthreads = TT) {
+  for (int e = threadIdx.x; e < rpad * cpad; e += nthreads) {
     const int r = e / cpad, c = e % cpad;
     const uint16_t v = (r < rows && c < cols) ? src[r * cols + c] : (uint16_t)0;
     *reinterpret_cast<uint16_t *>(dst + tc::core_off(r, c, rpad)) = v;
@@ -856,6 +860,345 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
 }
 
+// ---- forward with dedicated gather warps ---------------------------------------
+// Four MMA / epilogue warps (one thread a tile row, both column halves) run one tile's MLP
+// chain while eight gather warps (one thread a sample and level parity) interpolate the next
+// tile's features into the other of two feature buffers: full[b] hands buffer b to the chain,
+// and the commit of the layer-1 MMAs that read it (empty[b]) hands it back.  Two CTAs per SM
+// keep two chains in flight.  Results are those of the forward above: the same per-level
+// arithmetic, the same MMAs.
+constexpr int kWsMma = TM;                     // MMA / epilogue threads
+constexpr int kWsGather = 2 * TM;              // gather threads
+constexpr int kWsThreads = kWsMma + kWsGather;
+constexpr uint32_t kGatherBar = 2;  // named barrier of the gather warps
+
+template <int IN, bool VD>
+struct LW {
+  static constexpr int INP = L<IN, false, VD>::INP;
+  static constexpr int CIN = L<IN, false, VD>::CIN;
+  static constexpr int XL = 0;                  // [128 x 64] low parts of a layer's output
+  static constexpr int X = TM * 64 * 2;         // [128 x 64] high parts
+  static constexpr int FB = 2 * TM * 64 * 2;    // [2] features: high [128 x INP], then low
+  static constexpr int FBS = 2 * TM * INP * 2;  // bytes of one feature buffer
+  static constexpr int W1 = FB + 2 * FBS;       // weights, as in the layout above
+  static constexpr int W2 = W1 + 64 * INP * 2;
+  static constexpr int W3 = W2 + 64 * 64 * 2;
+  static constexpr int V1 = W3 + 16 * 64 * 2;
+  static constexpr int V2 = V1 + 64 * CIN * 2;
+  static constexpr int V3 = V2 + 64 * 64 * 2;
+  static constexpr int END = V3 + 16 * 64 * 2;
+  // mbarriers (MMA commit, full[2], empty[2]), TMEM address, abort flag
+  static constexpr int MISC = END;
+  static constexpr int SMEM = MISC + 64;
+  static constexpr uint32_t TCOLS = 128, C_DL = 64;
+};
+
+template <int IN, int G, bool COL, bool VD, int KL>
+__global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) {
+  constexpr int NM = kWsMma, NG = kWsGather;
+  using Y = LW<IN, VD>;
+  using A = L<IN, false, VD>;  // stored-activation offsets
+  constexpr int INP = Y::INP;
+  constexpr int CIN = Y::CIN;
+  constexpr int ACT = A::act_bytes(COL);
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + Y::MISC);
+  uint64_t *full = mbar + 1;   // [2] the gather warps filled feature buffer b
+  uint64_t *empty = mbar + 3;  // [2] the layer-1 MMAs that read feature buffer b completed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Y::MISC + 40);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Y::MISC + 48);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int r = 32 * (warp & 3) + lane;  // TMEM lane = tile row of an MMA / epilogue thread
+  const snk_state *st = a.state;
+  snk_state *st_rw = const_cast<snk_state *>(a.state);
+  const ModelDev &m = a.m;
+  const GridParams &gp = m.grid;
+  const uint32_t s0 = tc::smem_u32(sm);
+
+  if (t == 0) {
+    tc::mbar_init(mbar, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(full + b, NG);
+      tc::mbar_init(empty + b, 1);
+    }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, Y::TCOLS);
+  // zero every buffer once: the feature buffers' padding columns (IN .. INP-1) stay zero
+  for (int i = t; i < Y::END / 16; i += blockDim.x) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+
+  int64_t r0 = 0, r1 = st->slot_base[kMaxSlots];
+  if (a.slot_only >= 0) {
+    r0 = st->slot_base[a.slot_only];
+    r1 = r0 + st->slot_count[a.slot_only];
+  }
+  if (r1 > a.S) r1 = a.S;
+  const int64_t n_tiles = r1 > r0 ? (r1 - r0 + TM - 1) / TM : 0;
+
+  if (t >= NM) {
+    // ---- gather warps: tile j's features into buffer j & 1 ----
+    const int s = (t - NM) % TM, lq = (t - NM) / TM;  // sample of the tile, level parity
+    constexpr int LS = NG / TM;                        // level groups (2)
+    int j = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int64_t ts = r0 + tile * TM;
+      const int slot = slot_of(st, ts);
+      if (slot < 0) continue;  // the MMA warps skip the same tiles
+      const int b = j & 1;
+      if (j >= 2) {
+        // the layer-1 MMAs of tile j - 2 have read this buffer; every gather thread takes the
+        // same branch (the named barrier below needs all of them)
+        const int w = tc::mbar_wait_or_abort(empty + b, ((j >> 1) - 1) & 1, abort_flag);
+        if (w == 2) {
+          atomicOr(&st_rw->status, kStatusTimeout);
+          *abort_flag = 1;
+        }
+        if (tc::bar_or(kGatherBar, NG, w != 0)) break;
+      }
+      uint8_t *fh = sm + Y::FB + b * Y::FBS, *fl = fh + TM * INP * 2;
+      const int64_t slot_end = (int64_t)st->slot_base[slot] + st->slot_count[slot];
+      const int64_t sidx = ts + s;
+      const bool sval = sidx < slot_end && sidx < r1;
+      float xyz[3] = {0.f, 0.f, 0.f};
+      if (sval) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[sidx * 3 + q];
+      }
+      const __half2 *tab0 = reinterpret_cast<const __half2 *>(a.params_lp + (int64_t)slot * m.tile_params);
+      // KL levels per round: their corner loads are all issued before any is used
+      for (int l0 = lq; l0 < gp.L; l0 += LS * KL) {
+        __half2 hv[KL][8];
+        float fr[KL][3];
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+          const int l = l0 + LS * k;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) hv[k][c] = __float2half2_rn(0.f);
+          fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
+          if (l < gp.L && sval) {
+            const int N = gp.res[l];
+            const bool dense = gp.dense[l] != 0;
+            int ci[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[k][q]);
+            const __half2 *tab = tab0 + gp.offset[l];
+#pragma unroll
+            for (int c = 0; c < 8; c += 2)
+              load_pair(tab,
+                        grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
+                        grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                   (uint32_t)gp.T - 1u),
+                        hv[k][c], hv[k][c + 1]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+          const int l = l0 + LS * k;
+          if (l >= gp.L) break;
+          float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float w = ((c & 1) ? fr[k][0] : 1.0f - fr[k][0]) * ((c & 2) ? fr[k][1] : 1.0f - fr[k][1]) *
+                            ((c & 4) ? fr[k][2] : 1.0f - fr[k][2]);
+            const float2 v = __half22float2(hv[k][c]);
+            f0 = fmaf(w, v.x, f0);
+            f1 = fmaf(w, v.y, f1);
+          }
+          const uint32_t hp = pack_h2(f0, f1);
+          const float2 hh = unpack_h2(hp);
+          *reinterpret_cast<uint32_t *>(fh + tc::core_off(s, 2 * l, TM)) = hp;
+          *reinterpret_cast<uint32_t *>(fl + tc::core_off(s, 2 * l, TM)) =
+              pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
+        }
+      }
+      tc::bar_sync(kGatherBar, NG);
+      // the tile's features in the shared-memory layout, for the backward (high parts; low
+      // parts too unless the activations are stored)
+      uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);
+      for (int i = t - NM; i < TM * INP * 2 / 16; i += NG) {
+        __stcs(reinterpret_cast<uint4 *>(ftile) + i, reinterpret_cast<const uint4 *>(fh)[i]);
+        if (!a.acts) __stcs(reinterpret_cast<uint4 *>(ftile + TM * INP) + i, reinterpret_cast<const uint4 *>(fl)[i]);
+      }
+      tc::fence_async_smem();  // the features are read by the tensor core
+      tc::mbar_arrive(full + b);
+      ++j;
+    }
+  } else {
+    // ---- MMA / epilogue warps ----
+    uint32_t phase = 0;
+    bool abort = false;
+    int cur_slot = -1, j = 0;
+    auto sync_mma = [&]() -> bool {
+      const bool ok = tc::mbar_wait(mbar, phase);
+      if (ok) phase ^= 1u;
+      tc::fence_after_sync();
+      return !tc::bar_or(kChainBar, NM, !ok);
+    };
+    auto handoff = [&]() {
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      tc::bar_sync(kChainBar, NM);
+      tc::fence_after_sync();
+    };
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int64_t ts = r0 + tile * TM;
+      const int slot = slot_of(st, ts);
+      if (slot < 0) continue;
+      if (slot != cur_slot) {
+        tc::bar_sync(kChainBar, NM);
+        const uint16_t *P = a.params_lp + (int64_t)slot * m.tile_params;
+        const uint16_t *C = a.params_lp + m.colour_base + (m.shared_colour ? 0 : (int64_t)slot * m.colour_params);
+        load_weights(sm + Y::W1, P + m.w1, 64, IN, 64, INP, NM);
+        load_weights(sm + Y::W2, P + m.w2, 64, 64, 64, 64, NM);
+        load_weights(sm + Y::W3, P + m.w3, G, 64, 16, 64, NM);
+        if (COL) {
+          load_weights(sm + Y::V1, C + m.v1, 64, VD ? CIN : G, 64, CIN, NM);
+          load_weights(sm + Y::V2, C + m.v2, 64, 64, 64, 64, NM);
+          load_weights(sm + Y::V3, C + m.v3, 3, 64, 16, 64, NM);
+        }
+        cur_slot = slot;
+        handoff();
+      }
+      const int64_t slot_end = (int64_t)st->slot_base[slot] + st->slot_count[slot];
+      const int64_t idx = ts + r;
+      const bool valid = idx < slot_end && idx < r1;
+      uint8_t *gact = a.acts ? reinterpret_cast<uint8_t *>(a.acts) + (ts / TM) * (int64_t)ACT : nullptr;
+      const int b = j & 1;
+      // the gather warps' features of this tile; the barrier also orders the last tile's
+      // tensor-memory reads before this tile's MMAs
+      {
+        const int w = tc::mbar_wait_or_abort(full + b, (j >> 1) & 1, abort_flag);
+        tc::fence_before_sync();
+        abort = tc::bar_or(kChainBar, NM, w != 0);
+        tc::fence_after_sync();
+        if (abort) break;
+      }
+      const uint32_t fh = s0 + Y::FB + b * Y::FBS, fl = fh + TM * INP * 2;
+      if (t == 0) {
+        mma_fwd(tmem, fh, s0 + Y::W1, INP, 64);
+        mma_fwd(tmem + Y::C_DL, fl, s0 + Y::W1, INP, 64);
+        tc::commit(mbar);
+        tc::commit(empty + b);
+      }
+      ++j;
+      abort = !sync_mma();
+      if (abort) break;
+      for (int c = 0; c < 2; ++c)
+        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A1 : nullptr);
+      handoff();
+      if (t == 0) {
+        mma_fwd(tmem, s0 + Y::X, s0 + Y::W2, 64, 64);
+        mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W2, 64, 64);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      for (int c = 0; c < 2; ++c)
+        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A2 : nullptr);
+      handoff();
+      if (t == 0) {
+        mma_fwd(tmem, s0 + Y::X, s0 + Y::W3, 64, 16);
+        mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W3, 64, 16);
+        tc::commit(mbar);
+      }
+      abort = !sync_mma();
+      if (abort) break;
+      float g[16];
+      float rgb[3] = {0.f, 0.f, 0.f};
+      ld16_pair(trow, trow + Y::C_DL, g);
+      store16(sm + Y::X, sm + Y::XL, r, g, (COL && gact) ? gact + A::A3 : nullptr);
+      if (!COL) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rgb[k] = sigm(g[1 + k]);
+      }
+      if (VD) {
+        // colour input columns 16..31: SH of the sample's ray direction
+        float dir[3] = {0.f, 0.f, 1.f}, y[16];
+        if (valid) {
+          const uint32_t ray = a.smp_ray[idx];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) dir[q] = a.ray_od[(int64_t)(3 + q) * a.n_rays + ray];
+        }
+        sh16(dir[0], dir[1], dir[2], y);
+        store16(sm + Y::X + TM * 16 * 2, sm + Y::XL + TM * 16 * 2, r, y, gact ? gact + A::A3 + TM * 16 * 2 : nullptr);
+      }
+      handoff();
+      if (COL) {
+        if (t == 0) {
+          mma_fwd(tmem, s0 + Y::X, s0 + Y::V1, CIN, 64);
+          mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V1, CIN, 64);
+          tc::commit(mbar);
+        }
+        abort = !sync_mma();
+        if (abort) break;
+        for (int c = 0; c < 2; ++c)
+        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A4 : nullptr);
+        handoff();
+        if (t == 0) {
+          mma_fwd(tmem, s0 + Y::X, s0 + Y::V2, 64, 64);
+          mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V2, 64, 64);
+          tc::commit(mbar);
+        }
+        abort = !sync_mma();
+        if (abort) break;
+        for (int c = 0; c < 2; ++c)
+        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A5 : nullptr);
+        handoff();
+        if (t == 0) {
+          mma_fwd(tmem, s0 + Y::X, s0 + Y::V3, 64, 16);
+          mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V3, 64, 16);
+          tc::commit(mbar);
+        }
+        abort = !sync_mma();
+        if (abort) break;
+        float o[16];
+        ld16_pair(trow, trow + Y::C_DL, o);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rgb[k] = sigm(o[k]);
+      }
+      if (valid)
+        reinterpret_cast<float4 *>(a.sigma_rgb)[idx] = make_float4(__expf(g[0]), rgb[0], rgb[1], rgb[2]);
+    }
+    if (abort) {
+      if (t == 0) atomicOr(&st_rw->status, kStatusTimeout);
+      *abort_flag = 1;             // releases gather warps waiting for a buffer
+      tc::mbar_wait(mbar, phase);  // bounded: let any MMA still in flight finish before freeing TMEM
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, Y::TCOLS);
+}
+
+template <int IN, int G, bool COL, bool VD, int KL>
+cudaError_t launch_ws(const FieldArgs &a, int sm_count, cudaStream_t st) {
+  using Y = LW<IN, VD>;
+  static_assert(2 * (Y::SMEM + 1024) <= 233472, "two CTAs per SM: shared memory");
+  static_assert(2 * Y::TCOLS <= 512, "two CTAs per SM: tensor memory");
+  static_assert(Y::FB % 1024 == 0 && Y::FBS % 16 == 0 && Y::W1 % 16 == 0 && Y::MISC % 8 == 0, "alignment");
+  auto k = k_field_fws<IN, G, COL, VD, KL>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int64_t max_tiles = (a.S + TM - 1) / TM;
+  int64_t grid = (int64_t)sm_count * 2;
+  if (grid > max_tiles) grid = max_tiles;
+  if (grid <= 0) return cudaSuccess;
+  k<<<(unsigned)grid, kWsThreads, Y::SMEM, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <int IN, int G, bool COL, bool BWD, bool Q8, int KL, bool VD, int MINB, bool SV = false>
 cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_ctas) {
   using Y = L<IN, BWD, VD>;
@@ -888,6 +1231,13 @@ cudaError_t launch_mode(const FieldArgs &a, int sm_count, cudaStream_t st, const
     // stored activations (a training forward wrote them) or the forward recomputed
     if (a.acts) return launch_t<IN, G, COL, true, Q8, 1, VD, 1, true>(a, sm_count, st, 1);
     return launch_t<IN, G, COL, true, Q8, 1, VD, 1, false>(a, sm_count, st, 1);
+  }
+  // dedicated gather warps (the E4M3 forward reads its features: nothing to gather)
+  if constexpr (!Q8) {
+    if (tu.tc_fwd_split) {
+      if (tu.tc_fwd_levels == 2) return launch_ws<IN, G, COL, VD, 2>(a, sm_count, st);
+      return launch_ws<IN, G, COL, VD, 1>(a, sm_count, st);
+    }
   }
   // three CTAs per SM: compiled for at most 85 registers a thread
   if (tu.tc_fwd_ctas == 3) {

@@ -8,6 +8,7 @@ namespace snk {
 struct Tuning {
   int tc_fwd_ctas = 3;          // tensor-core forward: persistent CTAs per SM (1, 2, 3)
   int tc_fwd_levels = 1;        // tensor-core forward: levels whose corner loads are issued together (1, 2)
+  int tc_fwd_split = 1;         // tensor-core forward: dedicated gather warps, 2 CTAs per SM (0, 1)
   int tc_bwd_saved = 1;         // tensor-core training step: the forward stores activations for the backward (0, 1)
   int fp32_ctas = 2;            // binary32 field kernels: persistent CTAs per SM (1, 2)
   int composite_threads = 256;  // compositing: threads per block (64 .. 512, multiple of 32)

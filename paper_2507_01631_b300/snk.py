@@ -68,7 +68,7 @@ class SnkState(Structure):
 class SnkTuning(Structure):
     _fields_ = [("tc_fwd_ctas", c_int32), ("tc_fwd_levels", c_int32), ("fp32_ctas", c_int32),
                 ("composite_threads", c_int32), ("sampler_threads", c_int32), ("tuned", c_int32),
-                ("tc_bwd_saved", c_int32), ("reserved", c_int32)]
+                ("tc_bwd_saved", c_int32), ("tc_fwd_split", c_int32)]
 
 
 STRUCTS = [SnkCamera, SnkWindow, SnkModel, SnkLayout, SnkSampler, SnkAdam, SnkParams, SnkState, SnkTuning]
@@ -282,7 +282,10 @@ class Context:
     def set_tuning(self, **values):
         t = SnkTuning()
         self.call("snk_get_tuning", ctypes.byref(t))
+        names = {k for k, _ in SnkTuning._fields_}
         for k, v in values.items():
+            if k not in names:
+                raise KeyError("unknown launch-shape field %r" % k)
             setattr(t, k, int(v))
         self.call("snk_set_tuning", ctypes.byref(t))
 

@@ -43,6 +43,22 @@ def test_struct_sizes_match_the_binding(lib):
     assert lib.snk_version().startswith(b"libsnk")
 
 
+def test_struct_fields_match_the_binding():
+    """Field names and order of every struct in include/snk.h against the binding's mirror
+    (sizes alone miss two swapped or renamed fields of one type)."""
+    text = re.sub(r"/\*.*?\*/|//[^\n]*", "", open(os.path.join(ROOT, "include", "snk.h")).read(), flags=re.S)
+    structs = {name: body for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(snk_\w+);", text, flags=re.S)}
+    for cls in snk.STRUCTS:
+        cname = "snk_" + cls.__name__[3:].lower()
+        assert cname in structs, cname
+        fields = []
+        for decl in structs[cname].split(";"):
+            decl = decl.strip()
+            if decl:
+                fields += [re.sub(r"\[.*\]", "", v).strip().split()[-1].lstrip("*") for v in decl.split(",")]
+        assert fields == [f for f, _ in cls._fields_], (cname, fields)
+
+
 @pytest.mark.parametrize("name", list(W.WORKLOADS))
 def test_model_layout_matches_the_oracle(lib, name):
     w = W.get(name)

@@ -1,8 +1,9 @@
 """Launch shapes (snk_autotune / snk_set_tuning): every shape computes the same
 step -- rendered outputs bit-identical, gradients equal up to the order of
 float atomics; this includes the backward reading the forward's stored
-activations against recomputing them -- and the autotuner leaves the caller's
-training state alone."""
+activations against recomputing them, and the forward with dedicated gather
+warps against the one whose threads gather and then run the chain, for every
+model variant -- and the autotuner leaves the caller's training state alone."""
 import numpy as np
 import pytest
 
@@ -13,10 +14,14 @@ from paper_2507_01631_b300.trainer import Trainer, model_from_workload
 from gpu_util import make_case, normwise
 
 pytestmark = pytest.mark.gpu
-DEFAULT = dict(tc_fwd_ctas=2, tc_fwd_levels=1, tc_bwd_saved=1, fp32_ctas=2, composite_threads=256,
+DEFAULT = dict(tc_fwd_split=1, tc_fwd_ctas=2, tc_fwd_levels=1, tc_bwd_saved=1, fp32_ctas=2, composite_threads=256,
                sampler_threads=256)
-ALTERNATIVES = [("tc_fwd_ctas", 1), ("tc_fwd_ctas", 3), ("tc_fwd_levels", 2), ("tc_bwd_saved", 0), ("fp32_ctas", 1), ("composite_threads", 64),
-                ("composite_threads", 512), ("sampler_threads", 128), ("sampler_threads", 512)]
+# overrides of DEFAULT; the CTAs per SM matter only without the gather split
+ALTERNATIVES = [dict(tc_fwd_levels=2), dict(tc_fwd_split=0), dict(tc_fwd_split=0, tc_fwd_ctas=1),
+                dict(tc_fwd_split=0, tc_fwd_ctas=3), dict(tc_fwd_split=0, tc_fwd_levels=2),
+                dict(tc_fwd_split=0, tc_fwd_ctas=3, tc_fwd_levels=2), dict(tc_bwd_saved=0),
+                dict(tc_bwd_saved=0, tc_fwd_split=0), dict(fp32_ctas=1), dict(composite_threads=64),
+                dict(composite_threads=512), dict(sampler_threads=128), dict(sampler_threads=512)]
 
 
 @pytest.fixture(scope="module")
@@ -49,15 +54,29 @@ def test_every_launch_shape_computes_the_same_step(ctx, precision):
     case = make_case("window2x2_full", n_rays=384, crop=48, table_scale=0.3)
     ctx.set_tuning(**DEFAULT)
     out0, m0, loss0 = _step(ctx, case, precision)
-    for key, val in ALTERNATIVES + [("tc_fwd_ctas", (3, 2))]:
-        if val == (3, 2):  # three CTAs per SM with two levels of corner loads in flight
-            ctx.set_tuning(**dict(DEFAULT, tc_fwd_ctas=3, tc_fwd_levels=2))
-        else:
-            ctx.set_tuning(**dict(DEFAULT, **{key: val}))
+    for over in ALTERNATIVES:
+        ctx.set_tuning(**dict(DEFAULT, **over))
         out, m, loss = _step(ctx, case, precision)
-        assert np.array_equal(out, out0), (key, val)
-        assert abs(loss - loss0) <= 1e-6 * abs(loss0), (key, val)
-        assert normwise(m, m0) < 1e-5, (key, val)
+        assert np.array_equal(out, out0), over
+        assert abs(loss - loss0) <= 1e-6 * abs(loss0), over
+        assert normwise(m, m0) < 1e-5, over
+    ctx.set_tuning(**DEFAULT)
+
+
+@pytest.mark.parametrize("name", ["tiny_tile", "tile256_fp32", "tiny_window", "tiny_window_vd"])
+def test_gather_split_computes_the_same_step_for_every_model_variant(ctx, name):
+    """Density-only MLP (G = 4) at 8 and 16 features, colour network at 8 features, view
+    directions: the forward with dedicated gather warps against the other forward shapes."""
+    case = make_case(name, n_rays=384, crop=48, table_scale=0.3)
+    ctx.set_tuning(**DEFAULT)
+    out0, m0, loss0 = _step(ctx, case, snk.SNK_MIXED)
+    for over in [dict(tc_fwd_levels=2), dict(tc_fwd_split=0), dict(tc_fwd_split=0, tc_fwd_ctas=3),
+                 dict(tc_bwd_saved=0, tc_fwd_split=0), dict(tc_bwd_saved=0)]:
+        ctx.set_tuning(**dict(DEFAULT, **over))
+        out, m, loss = _step(ctx, case, snk.SNK_MIXED)
+        assert np.array_equal(out, out0), over
+        assert abs(loss - loss0) <= 1e-6 * abs(loss0), over
+        assert normwise(m, m0) < 1e-5, over
     ctx.set_tuning(**DEFAULT)
 
 
@@ -74,6 +93,7 @@ def test_autotune_picks_valid_shapes_and_leaves_the_training_state(ctx, precisio
     torch.cuda.synchronize()
     assert t["tuned"] == 1
     assert t["tc_fwd_ctas"] in (1, 2, 3) and t["tc_fwd_levels"] in (1, 2) and t["fp32_ctas"] in (1, 2)
+    assert t["tc_fwd_split"] in (0, 1) and t["tc_bwd_saved"] in (0, 1)
     assert t["composite_threads"] in (64, 128, 256, 512) and t["sampler_threads"] in (128, 256, 512)
     assert ctx.tuning() == t
     for a, b in zip(before, (tr.params, tr.grads, tr.m, tr.v, tr.steps, tr.state)):
@@ -86,8 +106,11 @@ def test_autotune_picks_valid_shapes_and_leaves_the_training_state(ctx, precisio
 
 
 def test_out_of_range_tuning_is_rejected(ctx):
-    for key, val in [("tc_fwd_ctas", 4), ("tc_fwd_levels", 4), ("tc_bwd_saved", 2), ("composite_threads", 96 + 1),
+    for key, val in [("tc_fwd_ctas", 4), ("tc_fwd_levels", 4), ("tc_bwd_saved", 2), ("tc_fwd_split", 2),
+                     ("composite_threads", 96 + 1),
                      ("sampler_threads", 1024), ("fp32_ctas", 0)]:
         with pytest.raises(RuntimeError):
             ctx.set_tuning(**dict(DEFAULT, **{key: val}))
+    with pytest.raises(KeyError):  # a misspelled field is not silently ignored
+        ctx.set_tuning(tc_fwd_splits=0)
     assert ctx.tuning()["tc_fwd_ctas"] == DEFAULT["tc_fwd_ctas"]
