@@ -434,8 +434,9 @@ int snk_tile_unpark(snk_ctx *ctx, const snk_model *model, const snk_params *p, i
 /* Launch shapes of the context's kernels (the paper has no counterpart: they
  * change speed, never results beyond the order of float atomics). */
 typedef struct {
-    int32_t tc_fwd_ctas;       /* tensor-core forward: persistent CTAs per SM, 1, 2 or 3 */
-    int32_t tc_fwd_levels;     /* tensor-core forward: levels whose corner loads are issued together, 1 or 2 */
+    int32_t tc_fwd_ctas;       /* tensor-core forward with tc_fwd_split = 0: persistent CTAs per SM, 1, 2 or 3 */
+    int32_t tc_fwd_levels;     /* tensor-core forward: levels whose corner loads a gathering thread issues
+                                  together, 1 or 2 */
     int32_t fp32_ctas;         /* binary32 field kernels: persistent CTAs per SM, 1 or 2 */
     int32_t composite_threads; /* compositing kernel: threads per block, 64..512, multiple of 32 */
     int32_t sampler_threads;   /* ray and sample kernels: threads per block, 128..512, multiple of 32 */
