@@ -70,8 +70,10 @@ __global__ void k_adam(const AdamArgs a) {
 }
 
 // The same update four parameters at a time (16-byte accesses); every group boundary and
-// L2 boundary is a multiple of 4, so the four share a group and an L2 flag.
-__global__ void k_adam4(const AdamArgs a) {
+// L2 boundary is a multiple of 4, so the four share a group and an L2 flag.  Each thread takes
+// two such groups a round and issues all eight loads before using any (the skip test is uniform
+// and rare, so the parameters are read even when it holds): more bytes in flight per thread.
+__global__ void __launch_bounds__(256, 4) k_adam4(const AdamArgs a) {
   __shared__ float bc1[9], bc2[9];
   bias_corrections(a, bc1, bc2);
   const bool skip = a.mixed && a.state->reserved[0] != 0u;
@@ -79,13 +81,10 @@ __global__ void k_adam4(const AdamArgs a) {
   const int64_t n4 = a.n / 4;
   float4 *P = reinterpret_cast<float4 *>(a.params), *G = reinterpret_cast<float4 *>(a.grads);
   float4 *M = reinterpret_cast<float4 *>(a.m), *V = reinterpret_cast<float4 *>(a.v);
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto update = [&](int64_t q, const float4 &gr, float4 &w, float4 &m, float4 &v) {
     const int64_t i = 4 * q;
     const int g = group_of(a, i);
-    const float4 gr = G[q];
-    G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (skip) continue;
-    float4 w = P[q], m = M[q], v = V[q];
     const bool mlp = i >= a.mlp_start[g];
     const float b1 = bc1[g], b2 = bc2[g];
     adam_one(a, gr.x, inv_scale, mlp, b1, b2, w.x, m.x, v.x);
@@ -100,6 +99,24 @@ __global__ void k_adam4(const AdamArgs a) {
       reinterpret_cast<uint2 *>(a.params_lp)[q] =
           make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
     }
+  };
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q0 < n4; q0 += 2 * stride) {
+    const int64_t q1 = q0 + stride;
+    const bool two = q1 < n4;
+    float4 g0 = G[q0], w0 = P[q0], m0 = M[q0], v0 = V[q0];
+    float4 g1 = zero, w1 = zero, m1 = zero, v1 = zero;
+    if (two) {
+      g1 = G[q1];
+      w1 = P[q1];
+      m1 = M[q1];
+      v1 = V[q1];
+    }
+    G[q0] = zero;
+    if (two) G[q1] = zero;
+    if (skip) continue;
+    update(q0, g0, w0, m0, v0);
+    if (two) update(q1, g1, w1, m1, v1);
   }
 }
 
