@@ -461,7 +461,10 @@ int snk_set_tuning(snk_ctx *ctx, const snk_tuning *in);
 /* Autotuner: time every candidate launch shape of the sampler, field-forward,
  * field-backward (binary32 path) and compositing kernels on this batch (CUDA
  * events on `stream`, one warm-up run and one or two timed runs each, one
- * stage at a time) and keep the fastest for every later call on ctx.  Reads
+ * stage at a time; tensor cores: per backward mode the fastest forward of
+ * tc_fwd_split 1, and 0 at 1, 2 or 3 CTAs per SM, each at 1 or 2 levels,
+ * then forward + backward pick the mode) and keep the fastest for every
+ * later call on ctx.  Reads
  * p->params / p->params_lp only: the caller's gradients, Adam state and step
  * state are untouched (the tuner allocates its own scratch gradient buffer and
  * state, and frees them).  Synchronises the stream; not graph-capturable.
