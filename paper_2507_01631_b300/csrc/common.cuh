@@ -190,6 +190,34 @@ __device__ __forceinline__ void load_pair(const __half2 *tab, uint32_t e0, uint3
   }
 }
 
+// One level of the FP16 hash-grid gather (Sec. 4.1, NGP features): the cell of point x at
+// resolution N (its fractions fr) and the feature pairs of its 8 corners, corner c at
+// (x + (c & 1), y + ((c >> 1) & 1), z + ((c >> 2) & 1)); tab holds the level's entries.
+__device__ __forceinline__ void gather_corners(const __half2 *tab, const float (&x)[3], int N, bool dense,
+                                               uint32_t Tmask, __half2 (&hv)[8], float (&fr)[3]) {
+  int ci[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) grid_cell(x[q], N, ci[q], fr[q]);
+#pragma unroll
+  for (int c = 0; c < 8; c += 2)
+    load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask),
+              grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask), hv[c], hv[c + 1]);
+}
+
+// Trilinear interpolation of the 8 corner feature pairs in binary32, corners summed in order.
+__device__ __forceinline__ float2 interp_corners(const __half2 (&hv)[8], const float (&fr)[3]) {
+  float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
+                    ((c & 4) ? fr[2] : 1.0f - fr[2]);
+    const float2 v = __half22float2(hv[c]);
+    f0 = fmaf(w, v.x, f0);
+    f1 = fmaf(w, v.y, f1);
+  }
+  return make_float2(f0, f1);
+}
+
 // grad[e0] += w0 * d, grad[e1] += w1 * d (fire-and-forget reductions).
 __device__ __forceinline__ void red_pair(float2 *grad, uint32_t e0, uint32_t e1, float w0, float w1, float2 d) {
   if ((e0 ^ e1) == 1u) {

@@ -535,35 +535,15 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 #pragma unroll
           for (int c = 0; c < 8; ++c) hv[k][c] = __float2half2_rn(0.f);
           fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
-          if (l < gp.L && sval) {
-            const int N = gp.res[l];
-            const bool dense = gp.dense[l] != 0;
-            int ci[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[k][q]);
-            const __half2 *tab = tab0 + gp.offset[l];
-#pragma unroll
-            for (int c = 0; c < 8; c += 2)
-              load_pair(tab,
-                        grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
-                        grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
-                                   (uint32_t)gp.T - 1u),
-                        hv[k][c], hv[k][c + 1]);
-          }
+          if (l < gp.L && sval)
+            gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
         }
 #pragma unroll
         for (int k = 0; k < KL; ++k) {
           const int l = l0 + 2 * k;
           if (l >= gp.L) break;
-          float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float w = ((c & 1) ? fr[k][0] : 1.0f - fr[k][0]) * ((c & 2) ? fr[k][1] : 1.0f - fr[k][1]) *
-                            ((c & 4) ? fr[k][2] : 1.0f - fr[k][2]);
-            const float2 v = __half22float2(hv[k][c]);
-            f0 = fmaf(w, v.x, f0);
-            f1 = fmaf(w, v.y, f1);
-          }
+          const float2 f = interp_corners(hv[k], fr[k]);
+          const float f0 = f.x, f1 = f.y;
           const uint32_t hp = pack_h2(f0, f1);
           const float2 hh = unpack_h2(hp);
           *reinterpret_cast<uint32_t *>(sm + Y::X0 + tc::core_off(s, 2 * l, TM)) = hp;
@@ -981,35 +961,15 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
 #pragma unroll
           for (int c = 0; c < 8; ++c) hv[k][c] = __float2half2_rn(0.f);
           fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
-          if (l < gp.L && sval) {
-            const int N = gp.res[l];
-            const bool dense = gp.dense[l] != 0;
-            int ci[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[k][q]);
-            const __half2 *tab = tab0 + gp.offset[l];
-#pragma unroll
-            for (int c = 0; c < 8; c += 2)
-              load_pair(tab,
-                        grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
-                        grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
-                                   (uint32_t)gp.T - 1u),
-                        hv[k][c], hv[k][c + 1]);
-          }
+          if (l < gp.L && sval)
+            gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
         }
 #pragma unroll
         for (int k = 0; k < KL; ++k) {
           const int l = l0 + LS * k;
           if (l >= gp.L) break;
-          float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float w = ((c & 1) ? fr[k][0] : 1.0f - fr[k][0]) * ((c & 2) ? fr[k][1] : 1.0f - fr[k][1]) *
-                            ((c & 4) ? fr[k][2] : 1.0f - fr[k][2]);
-            const float2 v = __half22float2(hv[k][c]);
-            f0 = fmaf(w, v.x, f0);
-            f1 = fmaf(w, v.y, f1);
-          }
+          const float2 f = interp_corners(hv[k], fr[k]);
+          const float f0 = f.x, f1 = f.y;
           const uint32_t hp = pack_h2(f0, f1);
           const float2 hh = unpack_h2(hp);
           *reinterpret_cast<uint32_t *>(fh + tc::core_off(s, 2 * l, TM)) = hp;

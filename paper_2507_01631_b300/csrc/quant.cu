@@ -31,29 +31,14 @@ __global__ void k_gather_amax(const FieldArgs a) {
       const int l = (int)(q % gp.L);
       slot = slot_of(a.state, idx);
       if (slot >= 0) {
-        const int N = gp.res[l];
-        const bool dense = gp.dense[l] != 0;
-        int ci[3];
-        float fr[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) grid_cell(a.xyz[idx * 3 + k], N, ci[k], fr[k]);
+        const float x[3] = {a.xyz[idx * 3], a.xyz[idx * 3 + 1], a.xyz[idx * 3 + 2]};
         const __half2 *tab = reinterpret_cast<const __half2 *>(a.params_lp + (int64_t)slot * a.m.tile_params) +
                              gp.offset[l];
         __half2 hv[8];
-#pragma unroll
-        for (int c = 0; c < 8; c += 2)
-          load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
-                    grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, (uint32_t)gp.T - 1u),
-                    hv[c], hv[c + 1]);
-        float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float w = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
-                          ((c & 4) ? fr[2] : 1.0f - fr[2]);
-          const float2 v = __half22float2(hv[c]);
-          f0 = fmaf(w, v.x, f0);
-          f1 = fmaf(w, v.y, f1);
-        }
+        float fr[3];
+        gather_corners(tab, x, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv, fr);
+        const float2 f = interp_corners(hv, fr);
+        const float f0 = f.x, f1 = f.y;
         reinterpret_cast<float2 *>(a.feat32)[idx * gp.L + l] = make_float2(f0, f1);
         m = fmaxf(fabsf(f0), fabsf(f1));
       }
