@@ -156,6 +156,13 @@ MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True, ""): 675.6, ("mixe
                             ("fp32", "field_backward", False, ""): 736.6, ("fp32", "field_forward", False, ""): 42.5}
 
 
+def dram_bytes_per_sample(prec_key, kernel, saved, split):
+    """Measured DRAM bytes per sample of a field kernel in the given configuration, or None
+    (no capture of that kernel as it stands)."""
+    shape = ("split" if split else "chain") if (kernel == "field_forward" and prec_key == "mixed") else ""
+    return MEASURED_DRAM_PER_SAMPLE.get((prec_key, kernel, bool(saved), shape))
+
+
 # ---- clocks -------------------------------------------------------------------
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -528,10 +535,7 @@ def run_ours(args, w):
         else:
             fl, by = 0, 0
         sm_max = pk.get("sm_max_mhz", 2032.0)
-        shape = ""
-        if name == "field_forward" and prec_key == "mixed":
-            shape = "split" if tuning.get("tc_fwd_split", 0) else "chain"
-        dram = MEASURED_DRAM_PER_SAMPLE.get((prec_key, name, saved, shape))
+        dram = dram_bytes_per_sample(prec_key, name, saved, tuning.get("tc_fwd_split", 0))
         traffic = dram * per_step_samples if dram is not None else None
         l2 = {"l2_gather_bytes_per_sample": w.L * 8 * w.F * (4 if args.precision == "fp32" else 2),
               "l2_red_bytes_per_sample": w.L * 8 * w.F * 4 * 2 if name == "field_backward" else 0}
