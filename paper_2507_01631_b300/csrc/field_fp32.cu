@@ -351,12 +351,8 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int ctas
   using D = Dims<IN, G, COL, VD>;
   const size_t smem = sizeof(float) * D::TOTAL;
   auto k = k_field_fp32<IN, G, COL, VD, MODE>;
-  static bool attr_done = false;  // per instantiation; the attribute is per device function
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint32_t> attr_done{0};  // per instantiation: devices whose limit is set
+  if (cudaError_t e = set_smem_limit(k, (int)smem, attr_done); e != cudaSuccess) return e;
   const int64_t max_tiles = (a.S + NS - 1) / NS;
   int64_t grid = (int64_t)sm_count * ctas_per_sm;
   if (grid > max_tiles) grid = max_tiles;

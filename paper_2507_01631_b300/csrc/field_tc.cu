@@ -1144,12 +1144,8 @@ cudaError_t launch_ws(const FieldArgs &a, int sm_count, cudaStream_t st) {
   static_assert(2 * Y::TCOLS <= 512, "two CTAs per SM: tensor memory");
   static_assert(Y::FB % 1024 == 0 && Y::FBS % 16 == 0 && Y::W1 % 16 == 0 && Y::MISC % 8 == 0, "alignment");
   auto k = k_field_fws<IN, G, COL, VD, KL>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint32_t> attr_done{0};  // per instantiation: devices whose limit is set
+  if (cudaError_t e = set_smem_limit(k, Y::SMEM, attr_done); e != cudaSuccess) return e;
   const int64_t max_tiles = (a.S + TM - 1) / TM;
   int64_t grid = (int64_t)sm_count * 2;
   if (grid > max_tiles) grid = max_tiles;
@@ -1169,12 +1165,8 @@ cudaError_t launch_t(const FieldArgs &a, int sm_count, cudaStream_t st, int fwd_
   static_assert(Y::MISC % 8 == 0 && 96 <= Y::SMEM - Y::MISC, "mbarriers and tile info in the MISC block");
   static_assert(Y::X0 % 16 == 0 && Y::X1 % 16 == 0 && Y::X3 % 16 == 0 && Y::X5 % 16 == 0, "bulk-copy targets");
   auto k = k_field_tc<IN, G, COL, BWD, Q8, KL, VD, MINB, SV>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Y::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static std::atomic<uint32_t> attr_done{0};  // per instantiation: devices whose limit is set
+  if (cudaError_t e = set_smem_limit(k, Y::SMEM, attr_done); e != cudaSuccess) return e;
   const int64_t max_tiles = (a.S + TM - 1) / TM;
   const int per_sm = BWD ? 1 : fwd_ctas;
   int64_t grid = (int64_t)sm_count * per_sm;

@@ -1,5 +1,7 @@
 // Internal interfaces between the translation units of libsnk.
 #pragma once
+#include <atomic>
+
 #include "common.cuh"
 
 namespace snk {
@@ -17,6 +19,21 @@ struct Tuning {
 
 // Adds n to the library-wide count of launched kernels (snk_launch_count).
 void count_launches(int n);
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once per
+// device (the attribute belongs to that device's context; `done` is the caller's per-kernel
+// mask of devices already set, devices >= 32 are set on every call).
+template <typename K>
+cudaError_t set_smem_limit(K kernel, int bytes, std::atomic<uint32_t> &done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint32_t bit = dev >= 0 && dev < 32 ? 1u << dev : 0u;
+  if (bit != 0u && (done.load(std::memory_order_acquire) & bit) != 0u) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // Workspace of one ray batch (context-owned, or caller buffers for the stage API).
 struct RayBuffers {
