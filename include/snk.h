@@ -17,6 +17,11 @@
  *    parameter says "host".  The library never frees caller memory.  The
  *    context owns only its workspace (snk_ctx_reserve) and its copy of the
  *    views (snk_set_views); snk_ctx_destroy frees both.
+ *  - A context belongs to the device given to snk_ctx_create.  Every other
+ *    call on it runs on the calling thread's current device, which must be
+ *    that device (and the stream one of its streams); snk_ctx_create and
+ *    snk_ctx_destroy make it current themselves.  Contexts on different
+ *    devices may live in one process.
  *  - Calls are asynchronous on the given stream (NULL = legacy default
  *    stream) unless they return a host value.  A call that needs more
  *    workspace than reserved grows it with cudaMalloc, which synchronises the
