@@ -227,13 +227,16 @@ def layout(model):
 
 
 class Context:
-    """Owns one snk_ctx on a device."""
+    """Owns one snk_ctx on a device.  Creating it makes that device current; later calls run
+    on the calling thread's current device, which must be the context's (torch.cuda.set_device
+    or torch.cuda.device(ctx.device) when several devices are in use)."""
 
     def __init__(self, device=0):
         self.lib = load()
         h = c_void_p()
         check(self.lib.snk_ctx_create(device, ctypes.byref(h)))
         self.h = h.value
+        self.device = int(device)
         self._keep = []
 
     def close(self):
