@@ -123,13 +123,19 @@ SIGNATURES = {
 STAGES = ("rays_segments_samples", "field_forward", "render_loss_backward", "field_backward", "adam")
 
 _lib = None
+_lib_path = None
 
 
-def load(path=LIB_PATH):
-    """Load libsnk.so (built by paper_2507_01631_b300.build) and declare signatures."""
-    global _lib
+def load(path=None):
+    """Load libsnk.so (built by paper_2507_01631_b300.build; path None = the in-tree one) and
+    declare signatures.  One library per process: once one is loaded, load() returns it, and
+    asking explicitly for another path is an error."""
+    global _lib, _lib_path
     if _lib is not None:
+        if path is not None and os.path.abspath(path) != _lib_path:
+            raise RuntimeError("libsnk already loaded from %s, not %s" % (_lib_path, os.path.abspath(path)))
         return _lib
+    path = os.path.abspath(LIB_PATH if path is None else path)
     if not os.path.exists(path):
         raise RuntimeError("libsnk.so not found at %s: run `python -m paper_2507_01631_b300.build`" % path)
     lib = ctypes.CDLL(path)
@@ -137,7 +143,7 @@ def load(path=LIB_PATH):
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
+    _lib, _lib_path = lib, path
     return lib
 
 

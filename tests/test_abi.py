@@ -129,3 +129,20 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.snk_ctx_destroy(None) == snk.SNK_OK
     assert lib.snk_sync_status(None, None, None) == snk.SNK_ERR_INVALID_ARG
     assert lib.snk_wait_selftest(None, 0, None, None) == snk.SNK_ERR_INVALID_ARG
+
+
+def test_a_missing_library_fails_loudly():
+    """No fallback: without libsnk.so the binding raises (fresh interpreter, nothing loaded)."""
+    import subprocess
+    import sys
+    code = ("from paper_2507_01631_b300 import snk\n"
+            "try:\n    snk.load('/nonexistent/libsnk.so')\nexcept RuntimeError as e:\n"
+            "    print('raised:', e)\n    raise SystemExit(0)\nraise SystemExit(1)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "not found" in r.stdout, (r.stdout, r.stderr)
+
+
+def test_one_library_per_process(lib):
+    assert snk.load() is lib
+    with pytest.raises(RuntimeError):
+        snk.load("/nonexistent/other/libsnk.so")
