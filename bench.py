@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--stage-timing", type=int, default=1)
     ap.add_argument("--autotune", type=int, default=1, help="pick the launch shapes on the first batch first")
     ap.add_argument("--red-ceiling", type=int, default=1,
-                    help="also time a stand-alone scatter of the step's table-gradient reductions")
+                    help="also time the stand-alone reduction probe (the peak of the reduction roofline)")
     return ap.parse_args()
 
 
@@ -78,7 +78,7 @@ def peaks():
     return d
 
 
-# ---- per-sample algorithmic work (see the design notes) ------------------------
+# ---- per-sample algorithmic work ----------------------------------------------------
 def mlp_flops_per_sample(w):
     IN, H, G = w.L * w.F, 64, w.geo_out
     CIN = G + (16 if w.view_dirs else 0)  # colour input: g, or [g | SH_16(direction)]
@@ -92,6 +92,40 @@ def act_bytes_per_sample(w):
     directions), c1, c2 (64 each)."""
     cin = w.geo_out + (16 if w.view_dirs else 0)
     return 2 * (128 + ((cin + 128) if w.colour else 0))
+
+
+def method_bytes_per_sample(w, precision, kernel):
+    """Algorithmic bytes per sample of the METHOD (independent of this implementation's
+    design): the hash-grid gather of S3 (8 corners x L levels x F features, 2 B each from the
+    FP16 tables, 4 B from binary32 ones), the scatter of S7c (8 corners x L x F binary32
+    gradient updates = 4 B each, counted once), and the per-sample streams the kernel must
+    read or write (xyz 12 B in; sigma, rgb 16 B out for the forward; dsigma, drgb 16 B in for
+    the backward).  The whole step adds both field kernels' figures minus the shared xyz
+    read plus the compositing's t, delta (8 B)."""
+    fb = 2 if precision != "fp32" else 4
+    gather = w.L * 8 * w.F * fb
+    scatter = w.L * 8 * w.F * 4
+    if kernel == "field_forward":
+        return gather + 12 + 16
+    if kernel == "field_backward":
+        return scatter + 12 + 16
+    if kernel == "step":
+        return gather + scatter + 12 + 8 + 16 + 16
+    return None
+
+
+def design_bytes_per_sample(w, precision, kernel, saved):
+    """Bytes per sample this implementation moves beyond the method's (its design choices):
+    the forward's feature store for the backward (split FP16, or high parts only with stored
+    activations), the stored activations, and their reads in the backward."""
+    if precision == "fp32":
+        return 0
+    IN = max(16, w.L * w.F)
+    feat = 2 * IN if saved else 4 * IN
+    acts = act_bytes_per_sample(w) if saved else 0
+    if kernel in ("field_forward", "field_backward"):
+        return feat + acts + (16 if (saved and kernel == "field_backward") else 0)
+    return None
 
 
 def field_backward_work(w, precision, saved=False):
@@ -148,6 +182,7 @@ def field_forward_work(w, precision, saved=False):
 # (tile-local traffic grows with the samples processed), keyed by (precision, kernel, stored
 # activations, forward shape: "split" = dedicated gather warps, "chain" = every thread gathers
 # then runs the chain); a kernel changed since its capture has no entry (traffic null).
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per sample of the 32768-ray capture of the 512 m tile x samples per launch"
 MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True, ""): 675.6, ("mixed", "field_backward", False, ""): 173.1,
                             ("mixed", "field_forward", True, "split"): 625.9,
                             ("mixed", "field_forward", False, "split"): 146.0,
@@ -233,6 +268,18 @@ def oracle_sample(w, cams, targets, params, seed, n_rays):
     return int(res.seg.ray_off[-1]), dt
 
 
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -277,7 +324,8 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "rays_per_step": args.cpu_rays, "precision": "fp64 oracle"},
             "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": "%d oracle steps of %d rays of %s" % (args.steps, args.cpu_rays, w.name)},
+                             "sample": "%d oracle steps of %d rays of %s" % (args.steps, args.cpu_rays, w.name),
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -339,47 +387,78 @@ def time_graph(torch, tr, batches, steps):
     return e0.elapsed_time(e1), int(sum(int(c.item()) & 0xFFFFFFFF for c in counts))
 
 
-def reduction_ceiling(torch, snk, ctx, w, pix, sampler, params, field_backward_ms):
-    """Time the library's stand-alone scatter (snk_encode_backward: one thread per sample and
-    level, full occupancy, nothing else running) on the samples of one batch: the rate at which
-    this GPU retires the step's table-gradient reductions (8 float2 per sample and level).  The
-    fused backward does the same reductions while it runs the MLP backward."""
-    import ctypes
-    from paper_2507_01631_b300.autograd import Stages
-    from paper_2507_01631_b300.trainer import model_from_workload
-    m32 = model_from_workload(w, snk.SNK_FP32)
-    st = Stages(ctx, m32, snk.window_struct(w.window()))
-    batch = st.sample(pix, sampler)
-    torch.cuda.synchronize()
-    extent = int(batch.state[11].item()) & 0xFFFFFFFF    # slot_base[4]: end of the slot-major samples
-    n_samples = int(batch.state[3].item()) & 0xFFFFFFFF
-    p = torch.from_numpy(np.asarray(params, np.float32)).cuda()
-    grads = torch.zeros_like(p)
-    dfeat = torch.randn(extent, w.L * w.F, device="cuda")
-    ps = snk.SnkParams(snk.ptr(p), None, snk.ptr(grads), None, None, None)
-
-    def run():
-        ctx.call("snk_encode_backward", ctypes.byref(m32), ctypes.byref(ps), snk.ptr(batch.smp_xyz),
-                 snk.ptr(batch.state), extent, snk.ptr(dfeat), None)
-    run()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(3):
-        run()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 3
-    reds = n_samples * w.L * 8
-    out = {"standalone_scatter_ms": ms, "reductions_per_step": reds, "standalone_reductions_per_s": reds / ms * 1e3,
-           "samples": n_samples}
-    if field_backward_ms:
-        out.update({"field_backward_ms": field_backward_ms, "fused_reductions_per_s": reds / field_backward_ms * 1e3,
-                    "fused_over_standalone": ms / field_backward_ms})
-    del dfeat, grads, batch
+def reduction_probe(torch, snk, ctx, n_entries, reps=3):
+    """Peak of the reduction roofline: the library's stand-alone reduction probe
+    (snk_l2_reduction_probe: nothing but fire-and-forget float reductions to random 16-byte
+    slots, full occupancy) on a table of one tile's gradient size (n_entries float2 entries),
+    timed with CUDA events after a warm-up.  Returns operations (= L2 sectors touched) per
+    second for 16-byte (v4) and 8-byte (v2) reductions."""
+    n16 = max(1, (int(n_entries) * 8) // 16)
+    table = torch.zeros(n16 * 4, dtype=torch.float32, device="cuda")
+    n_ops = 1 << 29
+    out = {"table_bytes": n16 * 16, "ops_per_call": n_ops}
+    for width in (16, 8):
+        ctx.call("snk_l2_reduction_probe", snk.ptr(table), n16, n_ops, width, 1, None)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for r in range(reps):
+            ctx.call("snk_l2_reduction_probe", snk.ptr(table), n16, n_ops, width, 2 + r, None)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["v4" if width == 16 else "v2"] = {"ms": ms, "ops_per_s": n_ops / ms * 1e3}
+    del table
     torch.cuda.empty_cache()
     return out
+
+
+# L2 reduction sectors per sample of the fused backward (ncu `lts__t_sectors_op_red.sum` over the
+# samples of the launch), keyed by (precision, stored activations); the capture's workload is named
+# beside it.  A kernel changed since its capture has no entry.
+MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (96.9, "tile512_full, 32768 rays")}
+
+
+def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=None):
+    """The dominant kernel's roofline: achieved = the method's algorithmic bytes per sample x
+    the samples of one launch / the launch's CUDA-event time, against the measured HBM peak;
+    beside it the tensor-pipe figure, the bytes this implementation adds by design, and (field
+    backward) the L2 reduction roofline against the probe's measured rate."""
+    method = method_bytes_per_sample(w, prec_key, name)
+    if method is None:
+        return {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    gbs = method * units / per_launch_s / 1e9
+    dram = dram_bytes_per_sample(prec_key, name, saved, split)
+    roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / pk["hbm_gbs"], "traffic": dram * units if dram is not None else None,
+            "peak_source": "%s hbm_gbs" % pk["source"], "algorithmic_bytes_per_sample": method,
+            "units_per_launch": units, "launch_ms": per_launch_s * 1e3}
+    design = design_bytes_per_sample(w, prec_key, name, saved)
+    if design:
+        roof["design_bytes_per_sample"] = design
+        roof["achieved_with_design_bytes"] = (method + design) * units / per_launch_s / 1e9
+    fl = (field_backward_work if name == "field_backward" else field_forward_work)(w, prec_key, saved)[0]
+    if prec_key == "fp32":
+        peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        roof["alu"] = {"achieved": fl * units / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                       "frac": fl * units / per_launch_s / 1e12 / peak,
+                       "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x max SM clock (derived)"}
+    else:
+        tfl = fl * units / per_launch_s / 1e12
+        roof["tensor"] = {"achieved": tfl, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                          "frac": tfl / pk["bf16_tflops_sustained"],
+                          "peak_source": "%s bf16_tflops_sustained (FP16 dense rate = BF16 rate)" % pk["source"]}
+    red = MEASURED_RED_SECTORS_PER_SAMPLE.get((prec_key, bool(saved)))
+    if name == "field_backward" and red is not None and probe:
+        sec = red[0] * units / per_launch_s
+        pv = probe["v4"]["ops_per_s"]
+        roof["l2_reduction"] = {"bound": "l2_red", "achieved": sec / 1e9, "peak": pv / 1e9, "unit": "G sectors/s",
+                                "frac": sec / pv, "sectors_per_sample": red[0],
+                                "peak_source": "snk_l2_reduction_probe, 16-byte reductions, measured in this run",
+                                "sectors_source": "ncu lts__t_sectors_op_red.sum per sample, %s" % red[1]}
+    return roof
 
 
 def run_ours(args, w):
@@ -488,21 +567,31 @@ def run_ours(args, w):
         gms, gs = time_graph(torch, tr, batches, args.steps)
         extra["graph_replay"] = {"value": gs / (gms / 1000.0), "unit": "samples/s", "ms_per_step": gms / args.steps,
                                  "steps": args.steps}
-    if args.red_ceiling and args.precision == "mixed":
-        fb = stages.get("field_backward")
-        extra["l2_reduction_ceiling"] = reduction_ceiling(torch, snk, ctx, w, batches[0], sampler, params,
-                                                          fb[0] / max(fb[1], 1) if fb else None)
+    probe = None
+    if args.red_ceiling:
+        probe = reduction_probe(torch, snk, ctx, snk.layout(model).n_entries)
+        extra["l2_reduction_probe"] = probe
     if args.compare_fp32 and args.precision == "mixed":
         m32 = model_from_workload(w, snk.SNK_FP32)
         tr32 = Trainer(ctx, m32, snk.window_struct(w.window()), sampler, params)
         if args.autotune:
             tr32.autotune(batches[0], stream=stream)
         tr32.train_step(batches[0], stream=stream)
+        ctx.stage_timing(True)
         fms, fs = time_steps(torch, tr32, batches, args.fp32_steps, stream)
+        st32 = ctx.stage_times()
+        ctx.stage_timing(False)
         rc32 = ctx.sync_status(tr32.state)
+        # its own roofline: the dominant stage (a per-tile field launch chain) against the
+        # binary32 ALU peak and, for the backward, the reduction probe
+        nm32, (ms32, calls32) = max(st32.items(), key=lambda kv: kv[1][0])
+        per32 = fs / args.fp32_steps
+        roof32 = roofline_of(w, "fp32", nm32, ms32 / max(calls32, 1) / 1000.0, per32, False, 0, peaks(), None)
         extra["fp32_per_tile"] = {"value": fs / (fms / 1000.0), "unit": "samples/s",
                                   "ms_per_step": fms / args.fp32_steps, "steps": args.fp32_steps, "status": rc32,
-                                  "launches": "one field launch per tile and direction, eager"}
+                                  "launches": "one field launch per tile and direction, eager",
+                                  "stage_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in st32.items()},
+                                  "roofline": roof32}
         del tr32
 
     t_max = ms
@@ -528,39 +617,16 @@ def run_ours(args, w):
         per_launch_s = (sms / max(calls, 1)) / 1000.0
         per_step_samples = n_samples / max(args.steps, 1)
         saved = bool(tuning.get("tc_bwd_saved", 0)) and prec_key != "fp32"
-        if name == "field_backward":
-            fl, by = field_backward_work(w, prec_key, saved)
-        elif name == "field_forward":
-            fl, by = field_forward_work(w, prec_key, saved)
-        else:
-            fl, by = 0, 0
-        sm_max = pk.get("sm_max_mhz", 2032.0)
-        dram = dram_bytes_per_sample(prec_key, name, saved, tuning.get("tc_fwd_split", 0))
-        traffic = dram * per_step_samples if dram is not None else None
-        l2 = {"l2_gather_bytes_per_sample": w.L * 8 * w.F * (4 if args.precision == "fp32" else 2),
-              "l2_red_bytes_per_sample": w.L * 8 * w.F * 4 * 2 if name == "field_backward" else 0}
-        if args.precision == "fp32" and fl:
-            peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
-            achieved = fl * per_step_samples / per_launch_s / 1e12
-            roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic,
-                    "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived)" % sm_max}
-        elif fl:
-            gbs = by * per_step_samples / per_launch_s / 1e9
-            tfl = fl * per_step_samples / per_launch_s / 1e12
-            hbm = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                   "frac": gbs / pk["hbm_gbs"], "peak_source": "%s hbm_gbs" % pk["source"]}
-            ten = {"bound": "tensor", "achieved": tfl, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                   "frac": tfl / pk["bf16_tflops_sustained"],
-                   "peak_source": "%s bf16_tflops_sustained (FP16 dense rate = BF16 rate)" % pk["source"]}
-            main, other = (hbm, ten) if hbm["frac"] >= ten["frac"] else (ten, hbm)
-            roof = dict(main)
-            roof.update({"kernel": name, "traffic": traffic, "other_bound": other})
-        else:
-            roof = {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None,
-                    "traffic": None}
-        roof.update(l2)
-        roof["traffic_source"] = "ncu DRAM bytes per sample of the 32768-ray capture x samples per launch"
+        if saved and st.get("bwd_mode") == 2:
+            saved = False  # the step fell back to recomputing its activations
+        roof = roofline_of(w, prec_key, name, per_launch_s, per_step_samples, saved, tuning.get("tc_fwd_split", 0),
+                           pk, probe)
+        step_bytes = method_bytes_per_sample(w, prec_key, "step")
+        step_s = (t_max / args.steps) / 1000.0
+        roof["step"] = {"algorithmic_bytes_per_sample": step_bytes,
+                        "achieved": step_bytes * per_step_samples / step_s / 1e9, "unit": "GB/s",
+                        "frac": step_bytes * per_step_samples / step_s / 1e9 / pk["hbm_gbs"]}
+        roof["traffic_source"] = TRAFFIC_SOURCE
         roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
 
     cpu = None
@@ -573,7 +639,8 @@ def run_ours(args, w):
             tot_t += t
         cpu = {"value": tot_s / tot_t, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": "2 oracle steps of %d rays of %s (%d samples), FP64 numpy" % (args.cpu_rays, w.name,
-                                                                                     int(tot_s))}
+                                                                                     int(tot_s)),
+               "nproc": os.cpu_count(), "cpu_model": cpu_model()}
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",

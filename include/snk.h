@@ -212,7 +212,12 @@ typedef struct {
     uint32_t iteration;  /* step counter, Philox key word of the stratified jitter */
     uint32_t slot_base[5];
     uint32_t slot_count[4];
-    uint32_t reserved[3];
+    uint32_t nonfinite;  /* internal: set during a step whose gradients are not all finite */
+    uint32_t bwd_mode;   /* backward of the last training step: 0 binary32 path, 1 the tensor-core
+                          * backward read the activations its forward stored, 2 it recomputed them
+                          * (the stored-activation buffer exceeded the context's activation budget
+                          * or could not be allocated, or tc_bwd_saved = 0) */
+    uint32_t reserved;
 } snk_state;
 
 /* ---- context ---------------------------------------------------------- */
@@ -223,6 +228,17 @@ int snk_ctx_create(int device, snk_ctx **out);
 int snk_ctx_destroy(snk_ctx *ctx);
 /* Size the workspace for batches of up to max_rays rays and max_samples samples. */
 int snk_ctx_reserve(snk_ctx *ctx, int64_t max_rays, int64_t max_samples);
+/* Most device memory (bytes) the context may hold for stored activations (the
+ * tensor-core training step's per-sample activations, 544 B a sample of sample
+ * capacity with a colour network).  A training step whose capacity needs more
+ * -- or whose buffer cudaMalloc cannot provide -- does not fail: it runs the
+ * backward that recomputes the forward's activations instead (the per-sample
+ * activations are recomputed instead of stored when batches outgrow memory;
+ * same results up to the order of float atomics), and writes 2 into
+ * snk_state.bwd_mode.  bytes < 0: no budget (the default; only cudaMalloc
+ * limits it).  A budget below the buffer the context already holds frees that
+ * buffer (synchronising the device). */
+int snk_ctx_set_act_budget(snk_ctx *ctx, int64_t bytes);
 /* Host only: the sample capacity a step of B rays with this window and sampler
  * sizes its workspace for (an upper bound of the batch's samples, Sec. 4.5:
  * K_ray a ray in uniform mode, else at most max(s K_min, (s - 1) K_min + K_ray)
@@ -251,6 +267,14 @@ int snk_model_layout(const snk_model *model, snk_layout *out);
  * views.  Sec. 4.3 (crops), Sec. 4.6 (rays from the cameras). */
 int snk_set_views(snk_ctx *ctx, const snk_camera *cams, int n_views, const float *const *crops,
                   snk_stream_t stream);
+
+/* FP16 working copy of a mixed-precision model's parameters: p->params_lp[i] =
+ * the binary32 p->params[i] rounded to the nearest FP16 (ties to even), for all
+ * n_params entries (snk_layout), on `stream`.  C12's working copy: a mixed
+ * model's first step needs it written once from the initial master weights
+ * (every training step refreshes it after Adam).  SNK_ERR_INVALID_ARG for a
+ * binary32 model or a NULL params / params_lp. */
+int snk_params_refresh_lp(snk_ctx *ctx, const snk_model *model, const snk_params *p, snk_stream_t stream);
 
 /* ---- stages ----------------------------------------------------------- */
 
@@ -321,7 +345,10 @@ int snk_composite_backward(snk_ctx *ctx, const float *sigma_rgb, const float *sm
  * samples of capacity and, on the tensor-core path with tc_bwd_saved (the
  * default), a stored-activation buffer for that capacity; the first step that
  * needs more allocates it (synchronising), so reserve before capturing a graph
- * and run one step eagerly.  SNK_ERR_OOM when an allocation fails. */
+ * and run one step eagerly.  SNK_ERR_OOM when the sample workspace cannot be
+ * allocated; a stored-activation buffer that exceeds the activation budget
+ * (snk_ctx_set_act_budget) or cannot be allocated is not an error: the step
+ * recomputes the activations in its backward (state->bwd_mode = 2). */
 int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, const uint32_t *pix, int B,
                    const snk_sampler *sampler, const snk_adam *adam, const snk_params *p, snk_state *state,
                    float *out, snk_stream_t stream);
@@ -350,10 +377,17 @@ int snk_quantize_e4m3(snk_ctx *ctx, const float *x, int64_t n, float scale, uint
  * file-scope device array of about 2.8 MB that every GPU which loads the
  * library holds until the process exits; nothing is allocated.
  *  - B may be at most 65536; larger batches return SNK_ERR_INVALID_ARG and a
- *    message in err (nullable, err_len bytes).
+ *    message in err (nullable, err_len bytes).  The window, sampler and
+ *    cameras are checked exactly as snk_set_views and snk_sample_segments
+ *    check them; occupancy culling is not offered (SNK_ERR_INVALID_ARG).
  *  - The first call on a device looks up the device address of the scratch on
- *    that device (the device current at the call); make that first call before
- *    any stream capture.
+ *    that device (the device current at the call).
+ *  - Calls cannot be captured into a CUDA graph: every call copies the cameras
+ *    from one static host staging array, which a replayed copy would read in
+ *    whatever state the latest call left it.  A call on a stream that is
+ *    capturing returns SNK_ERR_INVALID_ARG.  Calls queued on one stream
+ *    without synchronising in between are fine: each call's copy consumes the
+ *    staging array before the call returns.
  *  - Every call on a device shares the same scratch and leaves the last call's
  *    contents in it; nothing in it has to start at zero (each kernel writes what
  *    it later reads).  Calls that overlap on the GPU (other streams, other host
@@ -450,8 +484,11 @@ typedef struct {
                                   activations (FP16 high parts, 544 B a sample with a colour network, 576 B
                                   with view directions, 256 B without) in a context-owned buffer sized for
                                   the reserved samples, and the backward copies them back instead of
-                                  recomputing the forward; 0 the backward recomputes them.  Same results
-                                  either way (up to the order of float atomics). */
+                                  recomputing the forward, when that buffer fits the context's
+                                  activation budget (snk_ctx_set_act_budget) and can be allocated --
+                                  else the step recomputes them; 0 the backward recomputes them.  Same
+                                  results either way (up to the order of float atomics);
+                                  snk_state.bwd_mode records which ran. */
     int32_t tc_fwd_split;      /* tensor-core forward: 1 (default) eight gather warps a CTA interpolate the
                                   next tile's features while four MMA / epilogue warps run the current
                                   tile's MLP chain, two CTAs per SM (tc_fwd_ctas unused); 0 every thread
@@ -489,6 +526,20 @@ int snk_stage_timing(snk_ctx *ctx, int enable);
 /* Synchronise and return, per stage, the summed milliseconds and the number
  * of recorded calls since timing was enabled (ms, calls: n entries, n <= 5). */
 int snk_stage_times(snk_ctx *ctx, double *ms, int64_t *calls, int n);
+
+/* Reduction-rate probe (the paper has no counterpart: it measures the peak of the
+ * roofline that binds the hash-table gradient scatter).  Adds 1.0f with n_ops
+ * fire-and-forget reductions to slots of table, a caller-owned device array of
+ * n16 16-byte slots (n16 x 4 binary32, 16-byte aligned): operation i targets
+ * slot floor(h(i) n16 / 2^32), h a 32-bit multiplicative hash of i + seed, as
+ * one red.global.add.v4.f32 on the whole slot (width 16) or one .v2.f32 on half
+ * i mod 2 of it (width 8).  Nothing else runs in the kernel (full occupancy,
+ * grid-stride loop), so the caller's CUDA-event time of the call is the GPU's
+ * reduction rate for random addresses in a table of that size.  The table's sum
+ * grows by n_ops x width / 4.  SNK_ERR_INVALID_ARG for a NULL or misaligned
+ * table, n16 outside 1..2^32-1, n_ops < 0 or another width.  Asynchronous. */
+int snk_l2_reduction_probe(snk_ctx *ctx, float *table, int64_t n16, int64_t n_ops, int width, uint32_t seed,
+                           snk_stream_t stream);
 
 /* Wait for `stream` and report device-side status bits of `state` as a
  * status code (SNK_ERR_DEVICE_CHECK, SNK_ERR_TIMEOUT, SNK_ERR_OVERFLOW). */

@@ -10,7 +10,7 @@ Paper basis:
   segment ends fall exactly on tile faces; each segment is sampled
   separately; the face point belongs to both neighbouring segments.
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
 * acceptance = the ray's intersection with the scene box is non-empty and
   contained in its intersection with the window box;
 * segments split the scene-box interval at the interior planes of the window;

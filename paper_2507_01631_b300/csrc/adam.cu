@@ -19,7 +19,7 @@ __global__ void k_check_finite(const float *__restrict__ g, int64_t n, snk_state
   }
   for (int64_t i = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     bad |= !isfinite(g[i]);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&state->reserved[0], 1u);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&state->nonfinite, 1u);
 }
 
 // Per optimiser group: the bias corrections 1 - beta^t of its step t = steps + 1.
@@ -53,7 +53,7 @@ __device__ __forceinline__ float adam_one(const AdamArgs &a, float grad, float i
 __global__ void k_adam(const AdamArgs a) {
   __shared__ float bc1[9], bc2[9];
   bias_corrections(a, bc1, bc2);
-  const bool skip = a.mixed && a.state->reserved[0] != 0u;
+  const bool skip = a.mixed && a.state->nonfinite != 0u;
   const float inv_scale = a.mixed ? 1.0f / a.state->loss_scale : 1.0f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int g = group_of(a, i);
@@ -76,7 +76,7 @@ __global__ void k_adam(const AdamArgs a) {
 __global__ void __launch_bounds__(256, 4) k_adam4(const AdamArgs a) {
   __shared__ float bc1[9], bc2[9];
   bias_corrections(a, bc1, bc2);
-  const bool skip = a.mixed && a.state->reserved[0] != 0u;
+  const bool skip = a.mixed && a.state->nonfinite != 0u;
   const float inv_scale = a.mixed ? 1.0f / a.state->loss_scale : 1.0f;
   const int64_t n4 = a.n / 4;
   float4 *P = reinterpret_cast<float4 *>(a.params), *G = reinterpret_cast<float4 *>(a.grads);
@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(256, 4) k_adam4(const AdamArgs a) {
   }
 }
 
-// Bookkeeping after the update: step counts, loss scale, iteration counter.
-__global__ void k_step_end(snk_state *state, int32_t *steps, int n_groups, int mixed) {
-  const bool skip = mixed && state->reserved[0] != 0u;
+// Bookkeeping after the update: step counts, loss scale, iteration counter, the backward mode.
+__global__ void k_step_end(snk_state *state, int32_t *steps, int n_groups, int mixed, uint32_t bwd_mode) {
+  state->bwd_mode = bwd_mode;
+  const bool skip = mixed && state->nonfinite != 0u;
   if (skip) {
     state->status |= kStatusOverflow;
     state->loss_scale = fmaxf(state->loss_scale * 0.5f, 1.0f);
@@ -138,6 +139,13 @@ __global__ void k_step_end(snk_state *state, int32_t *steps, int n_groups, int m
     }
   }
   state->iteration += 1u;
+}
+
+// The FP16 working copy of binary32 parameters, round to nearest even (the conversion the Adam
+// kernels apply after each update).
+__global__ void k_refresh_lp(const float *__restrict__ w, uint16_t *__restrict__ lp, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    lp[i] = __half_as_ushort(__float2half_rn(w[i]));
 }
 
 }  // namespace
@@ -169,8 +177,15 @@ cudaError_t launch_adam(const AdamArgs &a, int sm_count, cudaStream_t st) {
     k_adam4<<<g_adam4, 256, 0, st>>>(a);
   else
     k_adam<<<g_adam, 256, 0, st>>>(a);
-  k_step_end<<<1, 1, 0, st>>>(a.state, a.steps, a.n_groups, a.mixed);
+  k_step_end<<<1, 1, 0, st>>>(a.state, a.steps, a.n_groups, a.mixed, a.bwd_mode);
   count_launches(a.mixed ? 3 : 2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_lp(const float *w, uint16_t *lp, int64_t n, int sm_count, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_refresh_lp<<<sm_count * 8, 256, 0, st>>>(w, lp, n);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ struct snk_ctx {
   size_t occ_ws_bytes = 0;
   void *acts = nullptr;        // stored activations of a tensor-core training step (tc_bwd_saved)
   size_t acts_bytes = 0;
+  int64_t act_budget = -1;     // most bytes acts may take (snk_ctx_set_act_budget); < 0: no budget
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -180,67 +181,8 @@ ModelDev model_dev(const snk_model *m, const snk_layout &lay) {
   return d;
 }
 
-int check_window(snk_ctx *ctx, const snk_window *w, int n_slots, WinParams *o) {
-  if (!w) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
-  if ((w->nx != 1 && w->nx != 2) || (w->ny != 1 && w->ny != 2))
-    return fail(ctx, SNK_ERR_INVALID_ARG, "window nx, ny must be 1 or 2");
-  if (w->nx * w->ny != n_slots)
-    return fail(ctx, SNK_ERR_INVALID_ARG, "window has %d tiles but the model has %d slots", w->nx * w->ny, n_slots);
-  int seen = 0;
-  for (int q = 0; q < n_slots; ++q) {
-    if (w->slot[q] < 0 || w->slot[q] >= n_slots || (seen >> w->slot[q]) & 1)
-      return fail(ctx, SNK_ERR_INVALID_ARG, "window slot[] must be a permutation of 0..%d", n_slots - 1);
-    seen |= 1 << w->slot[q];
-  }
-  for (int a = 0; a < 3; ++a) {
-    if (!(w->tile_size[a] > 0.0)) return fail(ctx, SNK_ERR_INVALID_ARG, "tile_size must be positive");
-    if (!(w->scene_hi[a] > w->scene_lo[a])) return fail(ctx, SNK_ERR_INVALID_ARG, "scene box is empty");
-  }
-  memset(o, 0, sizeof(*o));
-  for (int a = 0; a < 3; ++a) o->origin[a] = w->origin[a];
-  o->z_min = w->origin[2];
-  o->z_max = w->origin[2] + w->tile_size[2];
-  o->win_hi[0] = (float)(w->nx * w->tile_size[0]);
-  o->win_hi[1] = (float)(w->ny * w->tile_size[1]);
-  o->win_hi[2] = (float)w->tile_size[2];
-  for (int a = 0; a < 3; ++a) {
-    o->scene_lo[a] = (float)(w->scene_lo[a] - w->origin[a]);
-    o->scene_hi[a] = (float)(w->scene_hi[a] - w->origin[a]);
-    o->inv_size[a] = (float)(1.0 / w->tile_size[a]);
-  }
-  o->split[0] = (float)w->tile_size[0];
-  o->split[1] = (float)w->tile_size[1];
-  o->nx = w->nx;
-  o->ny = w->ny;
-  for (int q = 0; q < 4; ++q) o->slot[q] = q < n_slots ? w->slot[q] : 0;
-  o->n_slots = n_slots;
-  return SNK_OK;
-}
-
-int check_sampler(snk_ctx *ctx, const snk_sampler *s, SamplerParams *o) {
-  if (!s) return fail(ctx, SNK_ERR_INVALID_ARG, "sampler is NULL");
-  if (s->K_min < 1 || s->K_max < s->K_min || s->K_max > 4096 || s->K_ray < 1 || s->K_ray > 4096)
-    return fail(ctx, SNK_ERR_INVALID_ARG, "need 1 <= K_min <= K_max <= 4096 and 1 <= K_ray <= 4096");
-  o->K_ray = s->K_ray;
-  o->K_min = s->K_min;
-  o->K_max = s->K_max;
-  o->render = s->render ? 1 : 0;
-  o->seed = s->seed;
-  o->iteration = s->iteration;
-  o->use_state_iteration = 0;
-  if (s->occ_res < 0 || s->occ_res > 1024 || (s->occ_res > 0) != (s->occupancy != nullptr))
-    return fail(ctx, SNK_ERR_INVALID_ARG, "occupancy: need 1 <= occ_res <= 1024 with a grid, or occ_res 0 without");
-  o->occ_res = s->occ_res;
-  o->occ = s->occ_res > 0 ? s->occupancy : nullptr;
-  if (s->mode != SNK_SAMPLE_SEGMENTS && s->mode != SNK_SAMPLE_UNIFORM && s->mode != SNK_SAMPLE_POINTS)
-    return fail(ctx, SNK_ERR_INVALID_ARG, "sampler mode must be SNK_SAMPLE_SEGMENTS, _UNIFORM or _POINTS");
-  if (s->mode != SNK_SAMPLE_SEGMENTS && s->occ_res > 0)
-    return fail(ctx, SNK_ERR_INVALID_ARG, "occupancy culling needs SNK_SAMPLE_SEGMENTS");
-  if (s->mode == SNK_SAMPLE_POINTS && s->K_min < 2)
-    return fail(ctx, SNK_ERR_INVALID_ARG, "SNK_SAMPLE_POINTS needs K_min >= 2 (both segment ends)");
-  o->mode = s->mode;
-  return SNK_OK;
-}
+// The context's error text as the message sink of the shared descriptor checks.
+ErrSink sink(snk_ctx *ctx) { return ErrSink{ctx ? ctx->err : nullptr, ctx ? sizeof(ctx->err) : 0}; }
 
 size_t carve(size_t &off, size_t bytes) {
   const size_t o = off;
@@ -322,25 +264,36 @@ int64_t max_samples_for(const snk_window *w, const snk_sampler *s, int64_t B) {
   return B * per_ray + (int64_t)kSlotAlign * kMaxSlots;
 }
 
-// The stored-activation buffer of a tensor-core training step for the context's sample capacity.
-int ensure_acts(snk_ctx *ctx, const snk_model *model, cudaStream_t st) {
-  const size_t need = (size_t)(ctx->cap_samples / 128 + 1) * (size_t)act_tile_bytes(model->colour != 0, model->view_dirs != 0);
-  if (need <= ctx->acts_bytes) return SNK_OK;
+// Bytes of the stored-activation buffer of a tensor-core training step for the context's
+// sample capacity.
+size_t acts_need(const snk_ctx *ctx, const snk_model *model) {
+  return (size_t)(ctx->cap_samples / 128 + 1) * (size_t)act_tile_bytes(model->colour != 0, model->view_dirs != 0);
+}
+
+// The stored-activation buffer for the context's capacity, or nullptr when it exceeds the
+// activation budget or cannot be allocated: the step then recomputes the activations in its
+// backward (the per-sample activations are recomputed instead of stored when the batch
+// outgrows memory).  Not an error: nothing is written to the context's error text.
+uint16_t *acts_or_recompute(snk_ctx *ctx, const snk_model *model, cudaStream_t st) {
+  const size_t need = acts_need(ctx, model);
+  if (ctx->act_budget >= 0 && need > (size_t)ctx->act_budget) return nullptr;
+  if (need <= ctx->acts_bytes) return static_cast<uint16_t *>(ctx->acts);
   if (ctx->acts) {
-    SNK_CK(ctx, cudaStreamSynchronize(st));
-    SNK_CK(ctx, cudaFree(ctx->acts));
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaFree(ctx->acts);
     ctx->acts = nullptr;
     ctx->acts_bytes = 0;
   }
   if (cudaMalloc(&ctx->acts, need) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();  // not sticky: the recompute backward runs instead
     ctx->acts = nullptr;
-    return fail(ctx, SNK_ERR_OOM,
-                "stored activations of %zu bytes could not be allocated: reserve fewer samples or set "
-                "tc_bwd_saved = 0 (snk_set_tuning)", need);
+    return nullptr;
   }
   ctx->acts_bytes = need;
-  return SNK_OK;
+  return static_cast<uint16_t *>(ctx->acts);
 }
 
 int prepare(snk_ctx *ctx, const snk_model *model, snk_layout *lay, ModelDev *md) {
@@ -431,7 +384,30 @@ int snk_ctx_reserve(snk_ctx *ctx, int64_t max_rays, int64_t max_samples) {
   return ensure_ws(ctx, max_rays, max_samples);
 }
 
+int snk_ctx_set_act_budget(snk_ctx *ctx, int64_t bytes) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  ctx->act_budget = bytes < 0 ? -1 : bytes;
+  if (ctx->acts && bytes >= 0 && ctx->acts_bytes > (size_t)bytes) {
+    SNK_CK(ctx, cudaDeviceSynchronize());
+    SNK_CK(ctx, cudaFree(ctx->acts));
+    ctx->acts = nullptr;
+    ctx->acts_bytes = 0;
+  }
+  return SNK_OK;
+}
+
 const char *snk_last_error(const snk_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }
+
+int snk_params_refresh_lp(snk_ctx *ctx, const snk_model *model, const snk_params *p, snk_stream_t stream) {
+  snk_layout lay;
+  ModelDev md;
+  int rc = prepare(ctx, model, &lay, &md);
+  if (rc) return rc;
+  if (model->precision == SNK_FP32) return fail(ctx, SNK_ERR_INVALID_ARG, "snk_params_refresh_lp: a binary32 model has no working copy");
+  if (!p || !p->params || !p->params_lp) return fail(ctx, SNK_ERR_INVALID_ARG, "snk_params_refresh_lp: NULL params or params_lp");
+  SNK_CK(ctx, launch_refresh_lp(p->params, p->params_lp, lay.n_params, ctx->sm_count, (cudaStream_t)stream));
+  return SNK_OK;
+}
 
 int snk_set_views(snk_ctx *ctx, const snk_camera *cams, int n_views, const float *const *crops, snk_stream_t stream) {
   if (!ctx) return SNK_ERR_INVALID_ARG;
@@ -439,30 +415,9 @@ int snk_set_views(snk_ctx *ctx, const snk_camera *cams, int n_views, const float
     return fail(ctx, SNK_ERR_INVALID_ARG, "need 1..%d cameras", kMaxViews);
   SNK_CK(ctx, cudaStreamSynchronize((cudaStream_t)stream));  // the staging buffer may still be in flight
   for (int v = 0; v < n_views; ++v) {
-    const snk_camera &c = cams[v];
-    if (c.kind != SNK_CAM_AFFINE && c.kind != SNK_CAM_RPC3)
-      return fail(ctx, SNK_ERR_INVALID_ARG, "camera %d: unknown kind %d", v, c.kind);
-    if (c.crop_h < 0 || c.crop_w < 0 || c.crop_r0 < 0 || c.crop_c0 < 0 || c.crop_r0 + c.crop_h > 4096 ||
-        c.crop_c0 + c.crop_w > 4096)
-      return fail(ctx, SNK_ERR_INVALID_ARG, "camera %d: crop outside 0..4095", v);
-    if (c.kind == SNK_CAM_RPC3)
-      for (int q = 0; q < 3; ++q)
-        if (c.scale[q] == 0.0) return fail(ctx, SNK_ERR_INVALID_ARG, "camera %d: zero normalisation scale", v);
-    DevView &d = ctx->h_views[v];
-    memset(&d, 0, sizeof(d));
-    d.kind = c.kind;
-    d.width = c.width;
-    d.height = c.height;
-    d.crop_r0 = c.crop_r0;
-    d.crop_c0 = c.crop_c0;
-    d.crop_h = c.crop_h;
-    d.crop_w = c.crop_w;
-    memcpy(d.a, c.a, sizeof(d.a));
-    memcpy(d.b, c.b, sizeof(d.b));
-    memcpy(d.off, c.off, sizeof(d.off));
-    memcpy(d.scale, c.scale, sizeof(d.scale));
-    memcpy(d.coef, c.coef, sizeof(d.coef));
-    d.crop = crops ? crops[v] : nullptr;
+    const int rc = check_camera(sink(ctx), cams[v], v, &ctx->h_views[v]);
+    if (rc != SNK_OK) return rc;
+    ctx->h_views[v].crop = crops ? crops[v] : nullptr;
   }
   SNK_CK(ctx, cudaMemcpyAsync(ctx->d_views, ctx->h_views, sizeof(DevView) * n_views, cudaMemcpyHostToDevice,
                               (cudaStream_t)stream));
@@ -479,10 +434,10 @@ int snk_sample_segments(snk_ctx *ctx, const snk_window *win, const uint32_t *pix
   if (B < 0 || B > (1 << 22)) return fail(ctx, SNK_ERR_INVALID_ARG, "B must be in 0..2^22");
   if (!win) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
   WinParams wp;
-  int rc = check_window(ctx, win, win->nx * win->ny, &wp);
+  int rc = check_window(sink(ctx), win, win->nx * win->ny, &wp);
   if (rc) return rc;
   SamplerParams sp;
-  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  if ((rc = check_sampler(sink(ctx), sampler, &sp))) return rc;
   if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
   if (B > 0 && (!pix || !ray_od || !ray_ok || !seg_slot || !seg_t || !seg_n || !seg_off || !smp_t || !smp_dt ||
                 !smp_xyz || !state))
@@ -642,9 +597,11 @@ static RayBuffers step_rays(const snk_ctx *ctx, const snk_model *model) {
 
 // n_rays: the batch size of the rays whose directions ray_od holds ([6][n_rays]); every
 // sample's ray index (rb.smp_ray) is below it.
-// train: a training step (its forward stores activations for its backward when tc_bwd_saved).
+// acts: a training step's stored-activation buffer (its forward writes it, its backward reads
+// it back), or nullptr: no stored activations (the backward recomputes them).  Decided once
+// per step, so that the forward and backward of a step agree.
 static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, const snk_params *p,
-                     const snk_state *state, int mode, cudaStream_t st, int n_rays, bool train) {
+                     const snk_state *state, int mode, cudaStream_t st, int n_rays, uint16_t *acts) {
   FieldArgs fa{};
   fa.m = md;
   fa.params = p->params;
@@ -665,11 +622,7 @@ static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, c
   fa.n_rays = n_rays;
   if (model->precision != SNK_FP32) {
     fa.slot_only = -1;
-    if (train && ctx->tune.tc_bwd_saved) {
-      int rc = ensure_acts(ctx, model, st);
-      if (rc) return rc;
-      fa.acts = static_cast<uint16_t *>(ctx->acts);
-    }
+    fa.acts = acts;
     if (md.e4m3 && mode == kForward) {
       // the per-slot scales need every feature of the batch first
       SNK_CK(ctx, cudaMemsetAsync(ctx->amax, 0, sizeof(uint32_t) * kMaxSlots, st));
@@ -694,9 +647,9 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   int rc = prepare(ctx, model, &lay, &md);
   if (rc) return rc;
   WinParams wp;
-  if ((rc = check_window(ctx, win, model->n_slots, &wp))) return rc;
+  if ((rc = check_window(sink(ctx), win, model->n_slots, &wp))) return rc;
   SamplerParams sp;
-  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  if ((rc = check_sampler(sink(ctx), sampler, &sp))) return rc;
   sp.use_state_iteration = 1;
   sp.render = 0;
   if ((rc = check_params(ctx, model, p, true))) return rc;
@@ -705,6 +658,14 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   if (ctx->n_views < 1) return fail(ctx, SNK_ERR_INVALID_ARG, "no views: call snk_set_views first");
   if ((rc = ensure_ws(ctx, B, max_samples_for(win, sampler, B)))) return rc;
   const cudaStream_t st = (cudaStream_t)stream;
+  // backward mode of this step: stored activations when the buffer fits the budget and can be
+  // had, else recomputed
+  uint16_t *acts = nullptr;
+  uint32_t bwd_mode = 0;
+  if (model->precision != SNK_FP32) {
+    if (ctx->tune.tc_bwd_saved) acts = acts_or_recompute(ctx, model, st);
+    bwd_mode = acts ? 1u : 2u;
+  }
   {
     StageMark m(ctx, 0, st);
     SNK_CK(ctx, launch_sample_segments(ctx->d_views, ctx->n_views, wp, sp, pix, B, 1, step_rays(ctx, model), ctx->cap_samples, state,
@@ -712,7 +673,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   }
   {
     StageMark m(ctx, 1, st);
-    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B, true))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B, acts))) return rc;
   }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
@@ -733,7 +694,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   }
   {
     StageMark m(ctx, 3, st);
-    if ((rc = run_field(ctx, model, md, p, state, kBackward, st, B, true))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kBackward, st, B, acts))) return rc;
   }
   AdamArgs aa{};
   aa.params = p->params;
@@ -762,6 +723,7 @@ int snk_train_step(snk_ctx *ctx, const snk_model *model, const snk_window *win, 
   aa.l2 = adam->l2_mlp;
   aa.state = state;
   aa.mixed = model->precision != SNK_FP32;
+  aa.bwd_mode = bwd_mode;
   {
     StageMark m(ctx, 4, st);
     SNK_CK(ctx, launch_adam(aa, ctx->sm_count, st));
@@ -776,9 +738,9 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   int rc = prepare(ctx, model, &lay, &md);
   if (rc) return rc;
   WinParams wp;
-  if ((rc = check_window(ctx, win, model->n_slots, &wp))) return rc;
+  if ((rc = check_window(sink(ctx), win, model->n_slots, &wp))) return rc;
   SamplerParams sp;
-  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  if ((rc = check_sampler(sink(ctx), sampler, &sp))) return rc;
   sp.render = 1;
   if ((rc = check_params(ctx, model, p, false))) return rc;
   if (!state || !pix || !out || B < 1 || B > (1 << 22))
@@ -793,7 +755,7 @@ int snk_render(snk_ctx *ctx, const snk_model *model, const snk_window *win, cons
   }
   {
     StageMark m(ctx, 1, st);
-    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B, false))) return rc;
+    if ((rc = run_field(ctx, model, md, p, state, kForward, st, B, nullptr))) return rc;
   }
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
@@ -857,9 +819,9 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
   int rc = prepare(ctx, model, &lay, &md);
   if (rc) return rc;
   WinParams wp;
-  if ((rc = check_window(ctx, win, model->n_slots, &wp))) return rc;
+  if ((rc = check_window(sink(ctx), win, model->n_slots, &wp))) return rc;
   SamplerParams sp;
-  if ((rc = check_sampler(ctx, sampler, &sp))) return rc;
+  if ((rc = check_sampler(sink(ctx), sampler, &sp))) return rc;
   sp.render = 0;
   if ((rc = check_params(ctx, model, p, false))) return rc;
   if (!pix || B < 1 || B > (1 << 22)) return fail(ctx, SNK_ERR_INVALID_ARG, "need pix and 1 <= B <= 2^22");
@@ -903,7 +865,10 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
       return fail(ctx, SNK_ERR_CUDA, "snk_autotune: sampling failed");
     return SNK_OK;
   };
-  auto field = [&](int mode) { return run_field(ctx, model, md, &ps, state, mode, st, B, true); };
+  uint16_t *tune_acts = nullptr;  // the stored-activation buffer while the stored mode is timed
+  auto field = [&](int mode) {
+    return run_field(ctx, model, md, &ps, state, mode, st, B, ctx->tune.tc_bwd_saved ? tune_acts : nullptr);
+  };
   CompositeArgs ca{};
   ca.sigma_rgb = ctx->sigma_rgb;
   ca.smp_t = ctx->rb.smp_t;
@@ -940,7 +905,7 @@ int snk_autotune(snk_ctx *ctx, const snk_model *model, const snk_window *win, co
       double best_step = -1.0;
       snk::Tuning pick = ctx->tune;
       for (int sv : {1, 0}) {
-        if (sv == 1 && ensure_acts(ctx, model, st) != SNK_OK) continue;  // no room: recompute only
+        if (sv == 1 && (tune_acts = acts_or_recompute(ctx, model, st)) == nullptr) continue;  // no room: recompute only
         ctx->tune.tc_bwd_saved = sv;
         best = -1.0;
         int pc = saved.tc_fwd_ctas, pl = saved.tc_fwd_levels, ps = saved.tc_fwd_split;
@@ -1011,7 +976,7 @@ int snk_build_crops(snk_ctx *ctx, const snk_window *win, int margin, int32_t *ti
   if (!ctx) return SNK_ERR_INVALID_ARG;
   if (!win) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
   WinParams wp;
-  int rc = check_window(ctx, win, win->nx * win->ny, &wp);
+  int rc = check_window(sink(ctx), win, win->nx * win->ny, &wp);
   if (rc) return rc;
   if (!tile_rects || !view_rects || margin < 0 || margin > 4096)
     return fail(ctx, SNK_ERR_INVALID_ARG, "snk_build_crops: NULL output or margin outside 0..4096");
@@ -1029,7 +994,7 @@ int snk_ray_pool(snk_ctx *ctx, const snk_window *win, const int32_t *view_rects,
   if (!ctx) return SNK_ERR_INVALID_ARG;
   if (!win) return fail(ctx, SNK_ERR_INVALID_ARG, "window is NULL");
   WinParams wp;
-  int rc = check_window(ctx, win, win->nx * win->ny, &wp);
+  int rc = check_window(sink(ctx), win, win->nx * win->ny, &wp);
   if (rc) return rc;
   if (!view_rects || !pool || !n_pool || cap < 1 || cap > 0xFFFFFFFFll)
     return fail(ctx, SNK_ERR_INVALID_ARG, "snk_ray_pool: NULL buffer or cap outside 1..2^32-1");
@@ -1098,7 +1063,7 @@ int snk_occupancy_update(snk_ctx *ctx, const snk_model *model, const snk_params 
   const cudaStream_t st = (cudaStream_t)stream;
   SNK_CK(ctx, cudaMemsetAsync(state, 0, sizeof(snk_state), st));
   SNK_CK(ctx, launch_occ_points(model->n_slots, R, seed, step, ctx->rb.smp_xyz, ctx->rb.smp_ray, state, st));
-  if ((rc = run_field(ctx, model, md, p, state, kForward, st, 1, false))) return rc;
+  if ((rc = run_field(ctx, model, md, p, state, kForward, st, 1, nullptr))) return rc;
   SNK_CK(ctx, launch_occ_update(model->n_slots, R, ctx->sigma_rgb, decay, threshold, density, occupancy, partial, thr,
                                 st));
   return SNK_OK;
@@ -1129,6 +1094,17 @@ int snk_wait_selftest(snk_ctx *ctx, int arrive, snk_state *state, snk_stream_t s
   if (!ctx) return SNK_ERR_INVALID_ARG;
   if (!state) return fail(ctx, SNK_ERR_INVALID_ARG, "snk_wait_selftest: state is NULL");
   SNK_CK(ctx, launch_wait_selftest(arrive, state, (cudaStream_t)stream));
+  return SNK_OK;
+}
+
+int snk_l2_reduction_probe(snk_ctx *ctx, float *table, int64_t n16, int64_t n_ops, int width, uint32_t seed,
+                           snk_stream_t stream) {
+  if (!ctx) return SNK_ERR_INVALID_ARG;
+  if (!table || reinterpret_cast<uintptr_t>(table) % 16 != 0 || n16 < 1 || n16 > 0xFFFFFFFFll || n_ops < 0 ||
+      (width != 8 && width != 16))
+    return fail(ctx, SNK_ERR_INVALID_ARG,
+                "snk_l2_reduction_probe: need a 16-byte aligned table, 1 <= n16 < 2^32, n_ops >= 0, width 8 or 16");
+  SNK_CK(ctx, launch_red_probe(table, n16, n_ops, width, seed, ctx->sm_count, (cudaStream_t)stream));
   return SNK_OK;
 }
 

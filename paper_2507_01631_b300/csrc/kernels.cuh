@@ -20,6 +20,21 @@ struct Tuning {
 // Adds n to the library-wide count of launched kernels (snk_launch_count).
 void count_launches(int n);
 
+// Where a failing check writes its message (a context's error text, or a caller's buffer;
+// buf may be null): operator() formats the message and returns `code`.
+struct ErrSink {
+  char *buf;
+  size_t len;
+  int operator()(int code, const char *fmt, ...) const;
+};
+// Descriptor checks shared by every entry point that takes the descriptor (checks.cu):
+// SNK_OK with the kernel constants in *o, else SNK_ERR_INVALID_ARG and a message.
+int check_window(const ErrSink &fail, const snk_window *w, int n_slots, WinParams *o);
+int check_sampler(const ErrSink &fail, const snk_sampler *s, SamplerParams *o);
+// Camera v of a view list: kind, crop range, non-zero RPC normalisation scales; *d gets the
+// kernels' copy (crop pointer null).
+int check_camera(const ErrSink &fail, const snk_camera &c, int v, DevView *d);
+
 // Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once per
 // device (the attribute belongs to that device's context; `done` is the caller's per-kernel
 // mask of devices already set, devices >= 32 are set on every call).
@@ -161,7 +176,14 @@ struct AdamArgs {
   float lr, beta1, beta2, eps, l2;
   snk_state *state;
   int32_t mixed;
+  uint32_t bwd_mode;  // written to state->bwd_mode: 0 binary32, 1 stored activations, 2 recomputed
 };
 cudaError_t launch_adam(const AdamArgs &a, int sm_count, cudaStream_t st);
+// Diagnostic (probe.cu): n_ops reductions of `width` (8 or 16) bytes of 1.0f to random
+// 16-byte slots of table [n16][4] floats.
+cudaError_t launch_red_probe(float *table, int64_t n16, int64_t n_ops, int width, uint32_t seed, int sm_count,
+                             cudaStream_t st);
+// lp[i] = FP16(w[i]) (round to nearest even) for i < n: the mixed model's working copy.
+cudaError_t launch_refresh_lp(const float *w, uint16_t *lp, int64_t n, int sm_count, cudaStream_t st);
 
 }  // namespace snk

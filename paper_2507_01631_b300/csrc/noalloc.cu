@@ -39,8 +39,9 @@ std::mutex g_mutex;
 unsigned char *g_scratch_dev[kMaxDevices] = {nullptr};
 DevView g_views_host[kMaxViews];  // host staging, guarded by g_mutex
 
+// The caller's message buffer (nullable), prefixed with this entry point's name.
 int fail(char *err, int err_len, int code, const char *msg) {
-  if (err && err_len > 0) snprintf(err, (size_t)err_len, "%s", msg);
+  if (err && err_len > 0) snprintf(err, (size_t)err_len, "snk_sample_segments_static: %s", msg);
   return code;
 }
 
@@ -55,75 +56,42 @@ extern "C" int snk_sample_segments_static(const snk_window *win, const snk_camer
                                           int err_len) {
   using namespace snk;
   if (err && err_len > 0) err[0] = '\0';
+  char msg[256] = {0};
+  const ErrSink sink{msg, sizeof(msg)};
   if (B < 0 || B > kStaticMaxRays)
-    return fail(err, err_len, SNK_ERR_INVALID_ARG,
-                "snk_sample_segments_static: B must be in 0..65536 (the fixed scratch holds 65536 rays)");
-  if (!win || !sampler || !cams || n_views < 1 || n_views > kMaxViews)
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: NULL descriptor or 1..256 views");
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "B must be in 0..65536 (the fixed scratch holds 65536 rays)");
+  if (!cams || n_views < 1 || n_views > kMaxViews)
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "NULL cameras or not 1..256 views");
   if (B > 0 && (!pix || !ray_od || !ray_ok || !seg_slot || !seg_t || !seg_n || !seg_off || !smp_t || !smp_dt ||
                 !smp_xyz || !state))
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: NULL buffer");
-  if ((win->nx != 1 && win->nx != 2) || (win->ny != 1 && win->ny != 2))
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: window nx, ny must be 1 or 2");
-  const int n_slots = win->nx * win->ny;
-  int seen = 0;
-  for (int q = 0; q < n_slots; ++q) {
-    if (win->slot[q] < 0 || win->slot[q] >= n_slots || ((seen >> win->slot[q]) & 1))
-      return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: slot[] is not a permutation");
-    seen |= 1 << win->slot[q];
-  }
-  for (int a = 0; a < 3; ++a)
-    if (!(win->tile_size[a] > 0.0) || !(win->scene_hi[a] > win->scene_lo[a]))
-      return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: empty tile or scene box");
-  if (sampler->K_min < 1 || sampler->K_max < sampler->K_min || sampler->K_max > 4096 || sampler->K_ray < 1 ||
-      sampler->K_ray > 4096)
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: bad K_ray / K_min / K_max");
-  if (sampler->occ_res != 0 || sampler->occupancy != nullptr)
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: no occupancy culling (no scratch for it)");
-  for (int v = 0; v < n_views; ++v)
-    if (cams[v].kind != SNK_CAM_AFFINE && cams[v].kind != SNK_CAM_RPC3)
-      return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: unknown camera kind");
-
-  // binary32 window constants: correctly rounded from the binary64 descriptor
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "NULL buffer");
+  // the same descriptor checks and binary32 constants as snk_sample_segments
   WinParams wp;
-  memset(&wp, 0, sizeof(wp));
-  for (int a = 0; a < 3; ++a) wp.origin[a] = win->origin[a];
-  wp.z_min = win->origin[2];
-  wp.z_max = win->origin[2] + win->tile_size[2];
-  wp.win_hi[0] = (float)(win->nx * win->tile_size[0]);
-  wp.win_hi[1] = (float)(win->ny * win->tile_size[1]);
-  wp.win_hi[2] = (float)win->tile_size[2];
-  for (int a = 0; a < 3; ++a) {
-    wp.scene_lo[a] = (float)(win->scene_lo[a] - win->origin[a]);
-    wp.scene_hi[a] = (float)(win->scene_hi[a] - win->origin[a]);
-    wp.inv_size[a] = (float)(1.0 / win->tile_size[a]);
-  }
-  wp.split[0] = (float)win->tile_size[0];
-  wp.split[1] = (float)win->tile_size[1];
-  wp.nx = win->nx;
-  wp.ny = win->ny;
-  for (int q = 0; q < 4; ++q) wp.slot[q] = q < n_slots ? win->slot[q] : 0;
-  wp.n_slots = n_slots;
+  if (!win) return fail(err, err_len, SNK_ERR_INVALID_ARG, "window is NULL");
+  if (check_window(sink, win, win->nx * win->ny, &wp) != SNK_OK) return fail(err, err_len, SNK_ERR_INVALID_ARG, msg);
   SamplerParams sp;
-  sp.K_ray = sampler->K_ray;
-  sp.K_min = sampler->K_min;
-  sp.K_max = sampler->K_max;
-  sp.render = sampler->render ? 1 : 0;
-  sp.seed = sampler->seed;
-  sp.iteration = sampler->iteration;
-  sp.use_state_iteration = 0;
-  sp.occ_res = 0;
-  sp.occ = nullptr;
-  if (sampler->mode < SNK_SAMPLE_SEGMENTS || sampler->mode > SNK_SAMPLE_POINTS ||
-      (sampler->mode == SNK_SAMPLE_POINTS && sampler->K_min < 2))
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: bad sampler mode");
-  sp.mode = sampler->mode;
+  if (check_sampler(sink, sampler, &sp) != SNK_OK) return fail(err, err_len, SNK_ERR_INVALID_ARG, msg);
+  if (sp.occ_res != 0)
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "no occupancy culling (its per-segment counts have no scratch here)");
+  for (int v = 0; v < n_views; ++v) {
+    DevView tmp;
+    if (check_camera(sink, cams[v], v, &tmp) != SNK_OK) return fail(err, err_len, SNK_ERR_INVALID_ARG, msg);
+  }
+  // The camera copy below reads one static host staging array: a captured copy would replay
+  // whatever the latest call left there, so calls on a capturing stream are refused.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "the stream's capture status could not be read");
+  }
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "the stream is capturing a graph: calls cannot be captured");
 
   std::lock_guard<std::mutex> lock(g_mutex);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
-    return fail(err, err_len, SNK_ERR_CUDA, "snk_sample_segments_static: no current CUDA device");
+    return fail(err, err_len, SNK_ERR_CUDA, "no current CUDA device");
   }
   if (g_scratch_dev[dev] == nullptr) {
     // one-time set-up on this device (it is current): the scratch's device address
@@ -131,38 +99,21 @@ extern "C" int snk_sample_segments_static(const snk_window *win, const snk_camer
     const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
-      return fail(err, err_len, SNK_ERR_CUDA, "snk_sample_segments_static: cudaGetSymbolAddress failed");
+      return fail(err, err_len, SNK_ERR_CUDA, "cudaGetSymbolAddress failed");
     }
     g_scratch_dev[dev] = static_cast<unsigned char *>(p);
   }
   unsigned char *base = g_scratch_dev[dev];
   DevView *views = reinterpret_cast<DevView *>(base);
   if (B > 0 && scan_blocks(B) > kStaticMaxScanBlocks)
-    return fail(err, err_len, SNK_ERR_INVALID_ARG, "snk_sample_segments_static: batch exceeds the scan scratch");
+    return fail(err, err_len, SNK_ERR_INVALID_ARG, "batch exceeds the scan scratch");
 
-  for (int v = 0; v < n_views; ++v) {
-    const snk_camera &c = cams[v];
-    DevView &d = g_views_host[v];
-    memset(&d, 0, sizeof(d));
-    d.kind = c.kind;
-    d.width = c.width;
-    d.height = c.height;
-    d.crop_r0 = c.crop_r0;
-    d.crop_c0 = c.crop_c0;
-    d.crop_h = c.crop_h;
-    d.crop_w = c.crop_w;
-    memcpy(d.a, c.a, sizeof(d.a));
-    memcpy(d.b, c.b, sizeof(d.b));
-    memcpy(d.off, c.off, sizeof(d.off));
-    memcpy(d.scale, c.scale, sizeof(d.scale));
-    memcpy(d.coef, c.coef, sizeof(d.coef));
-    d.crop = nullptr;
-  }
+  for (int v = 0; v < n_views; ++v) check_camera(sink, cams[v], v, &g_views_host[v]);  // checked above
   // pageable source: the copy is staged before cudaMemcpyAsync returns, so the host staging can be reused
   if (cudaMemcpyAsync(views, g_views_host, sizeof(DevView) * n_views, cudaMemcpyHostToDevice,
                       (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();
-    return fail(err, err_len, SNK_ERR_CUDA, "snk_sample_segments_static: camera copy failed");
+    return fail(err, err_len, SNK_ERR_CUDA, "camera copy failed");
   }
   RayBuffers rb{};
   rb.ray_od = ray_od;

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(512) k_rays(const DevView *__restrict__ views,
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r == 0) {
     state->loss = 0.0f;
-    state->reserved[0] = 0u;  // non-finite-gradient flag of this step
+    state->nonfinite = 0u;  // non-finite-gradient flag of this step
   }
   if (r >= B) return;
   const uint32_t p = pix[r];

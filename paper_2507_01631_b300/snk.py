@@ -62,7 +62,8 @@ class SnkParams(Structure):
 class SnkState(Structure):
     _fields_ = [("loss", c_float), ("loss_scale", c_float), ("n_accepted", c_uint32), ("n_samples", c_uint32),
                 ("status", c_uint32), ("good_steps", c_int32), ("iteration", c_uint32),
-                ("slot_base", c_uint32 * 5), ("slot_count", c_uint32 * 4), ("reserved", c_uint32 * 3)]
+                ("slot_base", c_uint32 * 5), ("slot_count", c_uint32 * 4), ("nonfinite", c_uint32),
+                ("bwd_mode", c_uint32), ("reserved", c_uint32)]
 
 
 class SnkTuning(Structure):
@@ -83,6 +84,8 @@ SIGNATURES = {
     "snk_ctx_create": (c_int, [c_int, POINTER(c_void_p)]),
     "snk_ctx_destroy": (c_int, [_P]),
     "snk_ctx_reserve": (c_int, [_P, c_int64, c_int64]),
+    "snk_ctx_set_act_budget": (c_int, [_P, c_int64]),
+    "snk_params_refresh_lp": (c_int, [_P, POINTER(SnkModel), POINTER(SnkParams), _P]),
     "snk_max_samples": (c_int64, [POINTER(SnkWindow), POINTER(SnkSampler), c_int64]),
     "snk_last_error": (c_char_p, [_P]),
     "snk_set_views": (c_int, [_P, POINTER(SnkCamera), c_int, POINTER(c_void_p), _P]),
@@ -116,6 +119,7 @@ SIGNATURES = {
                                            POINTER(SnkSampler), _P, _P, _P, _P, _P, _P, _P, _P, _P, c_int64, _P, _P,
                                            c_char_p, c_int]),
     "snk_launch_count": (c_int64, []),
+    "snk_l2_reduction_probe": (c_int, [_P, _P, c_int64, c_int64, c_int, c_uint32, _P]),
     "snk_wait_selftest": (c_int, [_P, c_int, _P, _P]),
     "snk_stage_timing": (c_int, [_P, c_int]),
     "snk_stage_times": (c_int, [_P, POINTER(c_double), POINTER(c_int64), c_int]),
@@ -261,6 +265,11 @@ class Context:
 
     def reserve(self, max_rays, max_samples):
         self.call("snk_ctx_reserve", max_rays, max_samples)
+
+    def set_act_budget(self, nbytes):
+        """Most bytes of stored activations the context may hold (snk_ctx_set_act_budget); a
+        step that needs more recomputes them in its backward.  None or < 0: no budget."""
+        self.call("snk_ctx_set_act_budget", -1 if nbytes is None else int(nbytes))
 
     def max_samples(self, window, sampler, n_rays):
         """The sample capacity a step of n_rays rays sizes its workspace for (snk_max_samples)."""

@@ -9,7 +9,8 @@ import torch
 from . import snk
 
 STATE_FIELDS = {"loss": (0, "f"), "loss_scale": (1, "f"), "n_accepted": (2, "u"), "n_samples": (3, "u"),
-                "status": (4, "u"), "good_steps": (5, "i"), "iteration": (6, "u")}
+                "status": (4, "u"), "good_steps": (5, "i"), "iteration": (6, "u"), "bwd_mode": (17, "u")}
+BWD_MODES = {0: "binary32", 1: "stored activations", 2: "recomputed activations"}
 
 
 def model_from_workload(w, precision=None, hidden=64):
@@ -20,12 +21,6 @@ def model_from_workload(w, precision=None, hidden=64):
     prec = precision
     return snk.model_struct(w.L, w.F, w.log2_T, w.n_min, w.n_max, w.geo_out, w.colour, w.shared_colour,
                             w.n_slots, prec, hidden, view_dirs=getattr(w, "view_dirs", False))
-
-
-def low_precision_copy(params, lay, model):
-    """FP16 working copy of binary32 parameters (tables and MLP weights), as
-    int16 bit patterns in the flat layout."""
-    return params.to(torch.float16).view(torch.int16)
 
 
 class Trainer:
@@ -43,7 +38,8 @@ class Trainer:
         assert p.numel() == n, (p.numel(), n)
         self.params = p.contiguous()
         self.mixed = model.precision != snk.SNK_FP32
-        self.params_lp = low_precision_copy(self.params, self.lay, model) if self.mixed else None
+        # FP16 working copy (mixed precision): written by the library from the master weights
+        self.params_lp = torch.empty(n, dtype=torch.int16, device=device) if self.mixed else None
         self.grads = torch.zeros(n, dtype=torch.float32, device=device)
         self.m = torch.zeros(n, dtype=torch.float32, device=device)
         self.v = torch.zeros(n, dtype=torch.float32, device=device)
@@ -53,6 +49,14 @@ class Trainer:
         self.state.view(torch.float32)[1] = scale
         self.p_struct = snk.SnkParams(snk.ptr(self.params), snk.ptr(self.params_lp), snk.ptr(self.grads),
                                       snk.ptr(self.m), snk.ptr(self.v), snk.ptr(self.steps))
+        if self.mixed:
+            self.refresh_lp()
+
+    def refresh_lp(self, stream=None):
+        """Rewrite the FP16 working copy from the binary32 master weights (snk_params_refresh_lp),
+        e.g. after the caller changed self.params."""
+        self.ctx.call("snk_params_refresh_lp", ctypes.byref(self.model), ctypes.byref(self.p_struct),
+                      snk.stream_handle(stream))
 
     def train_step(self, pix, out=None, stream=None):
         self.ctx.call("snk_train_step", ctypes.byref(self.model), ctypes.byref(self.window), snk.ptr(pix),
@@ -74,6 +78,7 @@ class Trainer:
         out = {}
         for k, (i, t) in STATE_FIELDS.items():
             out[k] = float(s[i:i + 1].view(np.float32)[0]) if t == "f" else int(s[i:i + 1].view(np.uint32)[0])
+        out["bwd_mode_name"] = BWD_MODES.get(out["bwd_mode"], "?")
         out["slot_base"] = s[7:12].view(np.uint32).tolist()
         out["slot_count"] = s[12:16].view(np.uint32).tolist()
         return out

@@ -146,3 +146,33 @@ def test_one_library_per_process(lib):
     assert snk.load() is lib
     with pytest.raises(RuntimeError):
         snk.load("/nonexistent/other/libsnk.so")
+
+
+def test_static_sampler_refuses_bad_descriptors_before_any_cuda_call(lib):
+    """The allocation-free sampler checks its window, sampler and cameras with the same rules
+    as the context entry points (an RPC camera with a zero normalisation scale, a window whose
+    slots are not a permutation, occupancy culling it has no scratch for), before touching the
+    GPU: these run on a machine without one."""
+    from synth import workloads as W
+    w = W.get("tiny_window")
+    cams = W.cameras(w)
+    good = (snk.SnkCamera * len(cams))(*[snk.camera_struct(c) for c in cams])
+    sp = snk.sampler_struct(w.K_ray, w.K_min, w.K_max)
+    win = snk.window_struct(w.window())
+    err = ctypes.create_string_buffer(256)
+
+    def call(window, cam_arr, sampler):
+        return lib.snk_sample_segments_static(ctypes.byref(window), cam_arr, len(cams), None, 0, ctypes.byref(sampler),
+                                              *([None] * 9), 0, None, None, err, 256)
+    bad_cams = (snk.SnkCamera * len(cams))(*[snk.camera_struct(c) for c in cams])
+    bad_cams[1].kind = snk.SNK_CAM_RPC3
+    bad_cams[1].scale[2] = 0.0
+    assert call(win, bad_cams, sp) == snk.SNK_ERR_INVALID_ARG and b"zero normalisation scale" in err.value
+    bad_win = snk.window_struct(w.window())
+    bad_win.slot[1] = 0
+    assert call(bad_win, good, sp) == snk.SNK_ERR_INVALID_ARG and b"permutation" in err.value
+    occ = snk.sampler_struct(w.K_ray, w.K_min, w.K_max)
+    occ.occ_res, occ.occupancy = 8, 1
+    assert call(win, good, occ) == snk.SNK_ERR_INVALID_ARG and b"occupancy" in err.value
+    pts = snk.sampler_struct(w.K_ray, 1, w.K_max, mode=snk.SNK_SAMPLE_POINTS)
+    assert call(win, good, pts) == snk.SNK_ERR_INVALID_ARG and b"K_min >= 2" in err.value

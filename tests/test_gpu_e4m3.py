@@ -112,7 +112,9 @@ def test_train_step_e4m3_matches_oracle(ctx, name, n_rays, crop):
     assert st["n_samples"] == int(ref.seg.ray_off[-1]) and st["n_accepted"] == int(ref.seg.ray_ok.sum())
     amb = _ambiguous_rays(case, wc, ref)
     print("rays with a feature at an E4M3 tie: %d of %d" % (amb.sum(), B))
-    assert amb.mean() < 0.1
+    # decided by the oracle alone, so fixed by the seeds: 1 of 160 and 19 of 384 rays (about
+    # 6e-6 of the codes fall within two ulps of a tie; a ray of the window holds ~8300 codes)
+    assert amb.mean() <= 0.05, amb.sum()
     go = out.cpu().numpy().reshape(B, 5)
     keep = ~amb
     for nm, a, b in [("rgb", go[:, :3], ref.rgb), ("depth", go[:, 3], ref.depth), ("opacity", go[:, 4], ref.opacity)]:
@@ -146,7 +148,7 @@ def test_render_e4m3_matches_oracle(ctx, name, n_rays):
     wc = case.params.astype(np.float16).astype(np.float64)
     ref = OS.render_rays(case.cfg, wc, case.cams, case.w.window(), case.pix)
     amb = _ambiguous_rays(case, wc, ref)
-    assert amb.mean() < 0.1
+    assert amb.mean() <= 0.05, amb.sum()  # fixed by the seeds: 0 of 160 and 17 of 400 rays
     go = out.cpu().numpy().reshape(n_rays, 5)
     for nm, a, b in [("rgb", go[:, :3], ref.rgb), ("depth", go[:, 3], ref.depth), ("opacity", go[:, 4], ref.opacity)]:
         ok, err = close(a[~amb], b[~amb], RGB_REL_MIXED)

@@ -97,28 +97,33 @@ def mask_flip_deltas(case, ref, wc):
     return deltas
 
 
-def explain_with_flips(got, want, deltas, groups):
-    """Greedily add the flip deltas that bring `want` closer to `got`; returns the
-    adjusted reference."""
+MAX_FLIPS = 8  # accepted flips per step: a binary32 decision flips only within ~1e-7 of zero
+
+
+def explain_with_flips(got, want, deltas):
+    """Greedily add the flip deltas that bring `want` closer to `got`.  Returns the
+    adjusted reference and the norms of the accepted deltas relative to |want|.
+    The reference may move only by exact oracle flips of decisions that are
+    ambiguous in binary32, and by at most MAX_FLIPS of them (asserted by the caller)."""
     want = want.copy()
+    accepted = []
+    base = max(np.linalg.norm(want), 1e-300)
     for d in deltas:
         if np.linalg.norm(got - (want + d)) < np.linalg.norm(got - want):
             want = want + d
-    return want
+            accepted.append(float(np.linalg.norm(d) / base))
+    return want, accepted
 
 
 MIXED_CASES = [("tiny_tile", 96, None), ("tiny_window", 160, None), ("tile256_fp32", 512, None),
                ("tile512_full", 512, 48), ("window2x2_full", 512, 48)]
 
 
-@pytest.mark.parametrize("name,n_rays,crop", MIXED_CASES)
-def test_train_step_mixed_matches_oracle(ctx, name, n_rays, crop):
-    case = make_case(name, n_rays=n_rays, crop=crop, table_scale=0.3)
-    tr = _trainer(ctx, case)
-    B = n_rays
-    out = torch.zeros(B * 5, dtype=torch.float32, device="cuda")
-    tr.train_step(dev(case.pix.view(np.int32)), out)
-    assert ctx.sync_status(tr.state) == snk.SNK_OK
+def check_step_against_oracle(case, tr, out):
+    """The first mixed step of `tr` (rendered `out`) against the FP64 oracle on the working copy:
+    rendered rays, loss, every parameter group's gradient (via Adam's first moment) with the
+    ambiguous-ReLU flips accounted for, the first Adam move, the refreshed working copy."""
+    B = len(case.pix)
     st = tr.read_state()
     n = len(case.params)
     wc = working_copy(case.params, case.cfg)
@@ -135,8 +140,10 @@ def test_train_step_mixed_matches_oracle(ctx, name, n_rays, crop):
     m = tr.m.cpu().numpy().astype(np.float64)
     # decisions that may legitimately differ: account for flipped near-zero ReLU masks
     deltas = mask_flip_deltas(case, ref, wc)
-    ref_m = explain_with_flips(m, ref.m, [(1.0 - 0.9) * d for d in deltas], None)
-    print("ambiguous ReLU decisions:", len(deltas))
+    ref_m, flips = explain_with_flips(m, ref.m, [(1.0 - 0.9) * d for d in deltas])
+    print("ambiguous ReLU decisions: %d, accepted flips: %d, their sizes relative to |m|: %s"
+          % (len(deltas), len(flips), ["%.2e" % f for f in flips]))
+    assert len(flips) <= MAX_FLIPS, flips
     errs = {}
     for gi, (a, b, mlp_a) in enumerate(OS.group_ranges(case.cfg)):
         if mlp_a > a:
@@ -155,8 +162,60 @@ def test_train_step_mixed_matches_oracle(ctx, name, n_rays, crop):
     assert np.all(tr.grads.cpu().numpy() == 0)
     # the working copy was refreshed from the updated master weights
     lp = tr.params_lp.cpu()
-    from paper_2507_01631_b300.trainer import low_precision_copy
-    assert torch.equal(lp, low_precision_copy(tr.params.cpu(), tr.lay, tr.model))
+    assert torch.equal(lp, tr.params.cpu().to(torch.float16).view(torch.int16))
+    return st
+
+
+@pytest.mark.parametrize("name,n_rays,crop", MIXED_CASES)
+def test_train_step_mixed_matches_oracle(ctx, name, n_rays, crop):
+    case = make_case(name, n_rays=n_rays, crop=crop, table_scale=0.3)
+    tr = _trainer(ctx, case)
+    out = torch.zeros(n_rays * 5, dtype=torch.float32, device="cuda")
+    tr.train_step(dev(case.pix.view(np.int32)), out)
+    assert ctx.sync_status(tr.state) == snk.SNK_OK
+    check_step_against_oracle(case, tr, out)
+
+
+def test_activation_budget_switches_the_step_to_recompute(ctx):
+    """A budget smaller than the stored-activation buffer makes the step recompute the
+    activations in its backward instead of failing: the state reports the mode, the step
+    matches the oracle, and it computes what the stored mode computes (rendered outputs bit
+    for bit, moments up to the order of float atomics)."""
+    case = make_case("tile512_full", n_rays=512, crop=48, table_scale=0.3)
+    runs = {}
+    try:
+        for budget in (None, 4096):
+            ctx.set_act_budget(budget)
+            tr = _trainer(ctx, case)
+            out = torch.zeros(512 * 5, dtype=torch.float32, device="cuda")
+            tr.train_step(dev(case.pix.view(np.int32)), out)
+            assert ctx.sync_status(tr.state) == snk.SNK_OK
+            runs[budget] = (tr, out)
+    finally:
+        ctx.set_act_budget(None)
+    assert runs[None][0].read_state()["bwd_mode"] == 1
+    assert runs[4096][0].read_state()["bwd_mode"] == 2
+    assert torch.equal(runs[None][1], runs[4096][1])
+    assert normwise(runs[4096][0].m.cpu().numpy().astype(np.float64),
+                    runs[None][0].m.cpu().numpy().astype(np.float64)) < 1e-5
+    check_step_against_oracle(case, *runs[4096])
+
+
+def test_working_copy_is_written_by_the_library(ctx):
+    """snk_params_refresh_lp (called by the trainer) rounds every master weight to the nearest
+    FP16, ties to even, as torch's IEEE conversion does, including ties, overflow and
+    subnormals."""
+    case = make_case("tiny_window", n_rays=8, table_scale=0.3, with_targets=False)
+    params = case.params.copy()
+    special = np.array([1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, -(1 + 2.0 ** -11), 65504.0, 65520.0, -65536.0,
+                        2.0 ** -25, 3 * 2.0 ** -26, 1e-8, 2.0 ** -14, 0.0, -0.0], np.float32)
+    params[:len(special)] = special
+    case.params = params
+    tr = _trainer(ctx, case)
+    torch.cuda.synchronize()
+    want = torch.from_numpy(params).to(torch.float16).view(torch.int16)
+    assert torch.equal(tr.params_lp.cpu(), want)
+    assert tr.read_state()["bwd_mode"] == 0  # no step yet
 
 
 @pytest.mark.parametrize("name,n_rays", [("tiny_window", 160), ("tile512_full", 400), ("window2x2_full", 600)])

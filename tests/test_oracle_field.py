@@ -21,12 +21,31 @@ def test_level_layouts_of_the_workloads():
     assert np.all(np.abs(lay.res - 16 * b ** np.arange(16)) < 1.0)
 
 
-def test_spatial_hash_known_values():
-    T = 1 << 19
-    for (x, y, z) in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (3, 5, 7), (2047, 1, 2048), (4000, 4001, 4002)]:
-        expect = ((x * 1) % 2 ** 32 ^ (y * 2654435761) % 2 ** 32 ^ (z * 805459861) % 2 ** 32) % T
-        got = hashgrid.corner_index(np.array([x]), np.array([y]), np.array([z]), 0, False, T)[0]
-        assert got == expect
+# NGP's spatial hash at T = 2^19, worked out by hand for a few vertices: the uint32 products
+# y * 2654435761 and z * 805459861 (reduced mod 2^32), their xor with x, then the low 19 bits.
+HASH_T19 = [
+    # (x, y, z): y*Py mod 2^32, z*Pz mod 2^32, xor, index
+    ((1, 0, 0), 0, 0, 0x00000001, 1),
+    # 0x9e3779b1 & 0x7ffff = 0x779b1
+    ((0, 1, 0), 2654435761, 0, 0x9E3779B1, 489905),
+    # 0x30025795 & 0x7ffff = 0x25795
+    ((0, 0, 1), 0, 805459861, 0x30025795, 153493),
+    # 5 * 2654435761 = 13272178805 = 3 * 2^32 + 387276917; 7 * 805459861 = 5638219027 = 2^32 + 1343251731
+    ((3, 5, 7), 387276917, 1343251731, 0x47050565, 329061),
+    # 2048 * 805459861 = 1649581795328 = 384 * 2^32 + 314353664
+    ((2047, 1, 2048), 2654435761, 314353664, 0x8C8BD64E, 251470),
+    # 4001 * 2654435761 = 10620397479761 = 2472 * 2^32 + 3238324049;
+    # 4002 * 805459861 = 3223450363722 = 750 * 2^32 + 2224891722
+    ((4000, 4001, 4002), 3238324049, 2224891722, 0x4599CFBB, 118715),
+]
+
+
+@pytest.mark.parametrize("xyz,py,pz,h,index", HASH_T19)
+def test_spatial_hash_known_values(xyz, py, pz, h, index):
+    x, y, z = xyz
+    assert x ^ py ^ pz == h and h & ((1 << 19) - 1) == index    # the table is self-consistent
+    got = hashgrid.corner_index(np.array([x]), np.array([y]), np.array([z]), 0, False, 1 << 19)[0]
+    assert got == index
 
 
 def _trilinear_field(rng):
