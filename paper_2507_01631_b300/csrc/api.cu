@@ -39,6 +39,10 @@ struct snk_ctx {
   void *acts = nullptr;        // stored activations of a tensor-core training step (tc_bwd_saved)
   size_t acts_bytes = 0;
   int64_t act_budget = -1;     // most bytes acts may take (snk_ctx_set_act_budget); < 0: no budget
+  uint16_t *cells_lp = nullptr;  // mixed path: cell-major FP16 copy of the dense levels (rewritten before a forward)
+  size_t cells_lp_bytes = 0;
+  float *cell_grad = nullptr;    // mixed path: cell-major gradients of the dense levels (zero between steps)
+  size_t cell_grad_bytes = 0;
   snk::DevView *d_views = nullptr;
   snk::DevView *h_views = nullptr;  // pinned staging
   int n_views = 0;
@@ -154,11 +158,18 @@ ModelDev model_dev(const snk_model *m, const snk_layout &lay) {
   d.grid.F = m->F;
   d.grid.log2_T = m->log2_T;
   d.grid.T = 1 << m->log2_T;
+  uint32_t cells = 0;
   for (int l = 0; l < m->L; ++l) {
     d.grid.res[l] = lay.res[l];
     d.grid.dense[l] = lay.dense[l];
     d.grid.offset[l] = (uint32_t)lay.level_offset[l];
+    d.grid.cell_off[l] = cells;
+    if (lay.dense[l]) {
+      cells += (uint32_t)lay.res[l] * (uint32_t)lay.res[l] * (uint32_t)lay.res[l];
+      d.grid.dense_end = (uint32_t)(lay.level_offset[l] + lay.level_size[l]);
+    }
   }
+  d.grid.n_cells = cells;
   d.in_dim = m->L * m->F;
   d.geo_out = m->geo_out;
   d.colour = m->colour;
@@ -296,6 +307,61 @@ uint16_t *acts_or_recompute(snk_ctx *ctx, const snk_model *model, cudaStream_t s
   return static_cast<uint16_t *>(ctx->acts);
 }
 
+// The cell-major buffers of the dense levels for a mixed model (cells.cu): the FP16 copy the
+// forward gathers from and the gradient accumulator the backward scatters into.  A buffer that
+// cannot be allocated is not an error: the field kernels then use the table (and its gradient)
+// directly, with the same results.  The accumulator is cleared when allocated and kept clear by the
+// fold after each backward.
+uint16_t *cells_lp_for(snk_ctx *ctx, const ModelDev &md) {
+  const size_t need = (size_t)md.n_slots * md.grid.n_cells * 32;
+  if (need == 0) return nullptr;
+  if (need <= ctx->cells_lp_bytes) return ctx->cells_lp;
+  if (ctx->cells_lp) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaFree(ctx->cells_lp);
+    ctx->cells_lp = nullptr;
+    ctx->cells_lp_bytes = 0;
+  }
+  if (cudaMalloc(&ctx->cells_lp, need) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->cells_lp = nullptr;
+    return nullptr;
+  }
+  ctx->cells_lp_bytes = need;
+  return ctx->cells_lp;
+}
+
+float *cell_grad_for(snk_ctx *ctx, const ModelDev &md, cudaStream_t st) {
+  const size_t need = (size_t)md.n_slots * md.grid.n_cells * 64;
+  if (need == 0) return nullptr;
+  if (need <= ctx->cell_grad_bytes) return ctx->cell_grad;
+  if (ctx->cell_grad) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cudaFree(ctx->cell_grad);
+    ctx->cell_grad = nullptr;
+    ctx->cell_grad_bytes = 0;
+  }
+  if (cudaMalloc(&ctx->cell_grad, need) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->cell_grad = nullptr;
+    return nullptr;
+  }
+  if (cudaMemsetAsync(ctx->cell_grad, 0, need, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->cell_grad);
+    ctx->cell_grad = nullptr;
+    return nullptr;
+  }
+  ctx->cell_grad_bytes = need;
+  return ctx->cell_grad;
+}
+
 int prepare(snk_ctx *ctx, const snk_model *model, snk_layout *lay, ModelDev *md) {
   if (!ctx) return SNK_ERR_INVALID_ARG;
   const int rc = layout_of(model, lay, ctx->err, sizeof(ctx->err));
@@ -370,6 +436,8 @@ int snk_ctx_destroy(snk_ctx *ctx) {
   if (ctx->pool_ws) cudaFree(ctx->pool_ws);
   if (ctx->occ_ws) cudaFree(ctx->occ_ws);
   if (ctx->acts) cudaFree(ctx->acts);
+  if (ctx->cells_lp) cudaFree(ctx->cells_lp);
+  if (ctx->cell_grad) cudaFree(ctx->cell_grad);
   if (ctx->d_views) cudaFree(ctx->d_views);
   if (ctx->h_views) cudaFreeHost(ctx->h_views);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -628,7 +696,12 @@ static int run_field(snk_ctx *ctx, const snk_model *model, const ModelDev &md, c
       SNK_CK(ctx, cudaMemsetAsync(ctx->amax, 0, sizeof(uint32_t) * kMaxSlots, st));
       SNK_CK(ctx, launch_gather_amax(fa, ctx->sm_count, st));
     }
+    if (mode == kForward && !md.e4m3 && (fa.cells_lp = cells_lp_for(ctx, md)) != nullptr)
+      SNK_CK(ctx, launch_cells_copy(p->params_lp, md.tile_params, md.grid, md.n_slots, ctx->cells_lp, ctx->sm_count, st));
+    if (mode == kBackward) fa.cell_grad = cell_grad_for(ctx, md, st);
     SNK_CK(ctx, launch_field_tc(fa, ctx->sm_count, st, ctx->tune));
+    if (fa.cell_grad)
+      SNK_CK(ctx, launch_cells_fold(fa.cell_grad, p->grads, md.tile_params, md.grid, md.n_slots, ctx->sm_count, st));
     return SNK_OK;
   }
   // binary32 path: one launch chain per tile (slot), as a per-tile trainer issues them

@@ -57,11 +57,19 @@ constexpr int kSampleSegments = 0, kSampleUniform = 1, kSamplePoints = 2;
 
 
 // Grid level table passed by value to kernels.
+// Cell-major copies of the dense levels (mixed path): cell (x, y, z) of dense level l (x, y, z <
+// N_l) is cell cell_off[l] + x + N_l (y + N_l z) of a slot's n_cells cells, and holds its 8 corners
+// c = dx + 2 dy + 4 dz in order -- FP16 feature pairs (32 B a cell) for the forward's gather,
+// binary32 gradient pairs (64 B a cell) for the backward's scatter.  dense_end: the first table
+// entry after the last dense level (dense levels are the coarsest, a prefix of the levels).
 struct GridParams {
   int32_t L, F, log2_T, T;
   int32_t res[kMaxLevels];
   int32_t dense[kMaxLevels];
   uint32_t offset[kMaxLevels];
+  uint32_t cell_off[kMaxLevels];
+  uint32_t n_cells;
+  uint32_t dense_end;
 };
 
 // ---- exact binary32 / binary64 arithmetic (never contracted) --------------
@@ -202,6 +210,47 @@ __device__ __forceinline__ void gather_corners(const __half2 *tab, const float (
   for (int c = 0; c < 8; c += 2)
     load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask),
               grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask), hv[c], hv[c + 1]);
+}
+
+// One dense level from its cell-major FP16 copy (GridParams): the cell of point x at resolution N
+// (its fractions fr) and its 8 corner feature pairs, corner c = dx + 2 dy + 4 dz, in one 32-byte
+// load.  level_cells: the level's first cell (32-byte aligned blocks).
+__device__ __forceinline__ void gather_cell(const uint16_t *level_cells, const float (&x)[3], int N, __half2 (&hv)[8],
+                                            float (&fr)[3]) {
+  int ci[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) grid_cell(x[q], N, ci[q], fr[q]);
+  const uint32_t c = (uint32_t)ci[0] + (uint32_t)N * ((uint32_t)ci[1] + (uint32_t)N * (uint32_t)ci[2]);
+  uint32_t r[8];
+  asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "l"(level_cells + 16 * (size_t)c));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hv[q] = *reinterpret_cast<const __half2 *>(&r[q]);
+}
+
+// Segmented sums over the lanes of a warp (all 32 lanes call it): the runs of consecutive lanes
+// with equal `key` are the segments.  Afterwards the last lane of each run holds in v the sums of
+// its run's values, and the function returns true there.  Steps stop once no lane's run reaches
+// further back (a warp-uniform decision).
+template <int NV>
+__device__ __forceinline__ bool run_sums(float (&v)[NV], uint32_t key, int lane) {
+  const uint32_t up = __shfl_up_sync(0xffffffffu, key, 1), dn = __shfl_down_sync(0xffffffffu, key, 1);
+  const bool head = lane == 0 || up != key;
+  const bool tail = lane == 31 || dn != key;
+  const uint32_t heads = __ballot_sync(0xffffffffu, head);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this lane's run
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const bool take = lane - off >= start;
+    if (!__any_sync(0xffffffffu, take)) break;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float u = __shfl_up_sync(0xffffffffu, v[i], off);
+      if (take) v[i] += u;
+    }
+  }
+  return tail;
 }
 
 // Trilinear interpolation of the 8 corner feature pairs in binary32, corners summed in order.

@@ -375,34 +375,58 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     // weights, into the FP32 table gradients (float2 reductions, one thread per sample and
     // level group); they run while the MMA warps work on the next tile ----
     const int s = (t - TT) % TM, lq = (t - TT) / TM;  // sample of the tile, level group
+    const int lane = t & 31;                           // a warp: 32 consecutive samples, one level group
     int j = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       if (slot_of(st, r0 + tile * TM) < 0) continue;  // the MMA warps skip the same tiles
       const int b = j & 1;
       const int w = tc::mbar_wait_or_abort(full + b, (j >> 1) & 1, abort_flag);
-      if (w != 0) {
-        if (w == 2) {
-          atomicOr(&st_rw->status, kStatusTimeout);
-          *abort_flag = 1;
-        }
-        break;
+      if (w == 2) {
+        atomicOr(&st_rw->status, kStatusTimeout);
+        *abort_flag = 1;
       }
+      if (__any_sync(0xffffffffu, w != 0)) break;  // uniform over the warp: its lanes shuffle below
       const TileInfo ti = info[b];
-      if (s < ti.n_valid) {
-        const int64_t idx = ti.ts + s;
-        float xyz[3];
+      const bool sv = s < ti.n_valid;
+      const int64_t idx = ti.ts + s;
+      float xyz[3] = {0.f, 0.f, 0.f};
+      if (sv) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) xyz[q] = a.xyz[idx * 3 + q];
-        const float *dfr = dfbuf + (b * TM + s) * Y::DFS;
-        float2 *gt0 = reinterpret_cast<float2 *>(a.grads + (int64_t)ti.slot * m.tile_params);
-        for (int l = lq; l < gp.L; l += TS / TM) {
-          const int N = gp.res[l];
-          const bool dense = gp.dense[l] != 0;
-          int ci[3];
-          float fr[3];
+      }
+      const float *dfr = dfbuf + (b * TM + s) * Y::DFS;
+      float2 *gt0 = reinterpret_cast<float2 *>(a.grads + (int64_t)ti.slot * m.tile_params);
+      for (int l = lq; l < gp.L; l += TS / TM) {
+        const int N = gp.res[l];
+        const bool dense = gp.dense[l] != 0;
+        int ci[3];
+        float fr[3];
 #pragma unroll
-          for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
-          const float2 d = *reinterpret_cast<const float2 *>(dfr + 2 * l);
+        for (int q = 0; q < 3; ++q) grid_cell(xyz[q], N, ci[q], fr[q]);
+        const float2 d = sv ? *reinterpret_cast<const float2 *>(dfr + 2 * l) : make_float2(0.f, 0.f);
+        if (dense && a.cell_grad) {
+          // dense level: the warp's samples that share a cell (consecutive samples along a ray)
+          // sum their 8 corner terms first; the run's last lane adds them to the cell's 64-byte
+          // block of the cell-major accumulator in four 16-byte reductions
+          const uint32_t key = sv ? (uint32_t)ci[0] + (uint32_t)N * ((uint32_t)ci[1] + (uint32_t)N * (uint32_t)ci[2])
+                                  : 0xffffffffu;
+          float v[16];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float wc = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
+                             ((c & 4) ? fr[2] : 1.0f - fr[2]);
+            v[2 * c] = wc * d.x;
+            v[2 * c + 1] = wc * d.y;
+          }
+          if (run_sums(v, key, lane) && sv) {
+            float *q = a.cell_grad + ((int64_t)ti.slot * gp.n_cells + gp.cell_off[l] + key) * 16;
+#pragma unroll
+            for (int k = 0; k < 16; k += 4)
+              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(q + k), "f"(v[k]), "f"(v[k + 1]),
+                           "f"(v[k + 2]), "f"(v[k + 3])
+                           : "memory");
+          }
+        } else if (sv) {
           float2 *gt = gt0 + gp.offset[l];
           // corners c and c + 1 differ in x only; red_pair merges them when they share an aligned pair
 #pragma unroll
@@ -535,8 +559,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 #pragma unroll
           for (int c = 0; c < 8; ++c) hv[k][c] = __float2half2_rn(0.f);
           fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
-          if (l < gp.L && sval)
-            gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
+          if (l < gp.L && sval) {
+            if (a.cells_lp && gp.dense[l])  // one 32-byte load from the cell-major copy
+              gather_cell(a.cells_lp + ((int64_t)slot * gp.n_cells + gp.cell_off[l]) * 16, xyz, gp.res[l], hv[k], fr[k]);
+            else
+              gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
+          }
         }
 #pragma unroll
         for (int k = 0; k < KL; ++k) {
@@ -961,8 +989,12 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
 #pragma unroll
           for (int c = 0; c < 8; ++c) hv[k][c] = __float2half2_rn(0.f);
           fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
-          if (l < gp.L && sval)
-            gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
+          if (l < gp.L && sval) {
+            if (a.cells_lp && gp.dense[l])  // one 32-byte load from the cell-major copy
+              gather_cell(a.cells_lp + ((int64_t)slot * gp.n_cells + gp.cell_off[l]) * 16, xyz, gp.res[l], hv[k], fr[k]);
+            else
+              gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
+          }
         }
 #pragma unroll
         for (int k = 0; k < KL; ++k) {

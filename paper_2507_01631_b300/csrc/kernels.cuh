@@ -103,6 +103,9 @@ struct FieldArgs {
   uint8_t *codes;             // E4M3 path: [S][IN] first-layer codes (forward writes, backward reads)
   uint32_t *amax;             // E4M3 path: per slot, bits of max |feature| of the step (>= 0 floats)
   uint16_t *acts;             // tensor-core training step: stored activations, act_tile_bytes a tile, or null
+  const uint16_t *cells_lp;   // mixed forward: cell-major FP16 copy of the dense levels ([n_slots][n_cells][8] pairs), or null
+  float *cell_grad;           // mixed backward: cell-major binary32 gradients of the dense levels ([n_slots][n_cells][8]
+                              // pairs; zero between steps), or null (dense levels then add into grads directly)
   const uint32_t *smp_ray;    // view-direction models: [S] ray of each sample
   const float *ray_od;        // view-direction models: [6][n_rays] ray origins and directions
   int32_t n_rays;
@@ -183,6 +186,13 @@ cudaError_t launch_adam(const AdamArgs &a, int sm_count, cudaStream_t st);
 // 16-byte slots of table [n16][4] floats.
 cudaError_t launch_red_probe(float *table, int64_t n16, int64_t n_ops, int width, uint32_t seed, int sm_count,
                              cudaStream_t st);
+// Cell-major copies of the dense levels (cells.cu): the FP16 corner pairs of every cell of every
+// slot's dense levels from the working copy; and the fold of the cell-major gradients into the
+// table gradients (each vertex sums the corners it is of its up to 8 cells), clearing them.
+cudaError_t launch_cells_copy(const uint16_t *params_lp, int64_t tile_params, const GridParams &gp, int n_slots,
+                              uint16_t *cells, int sm_count, cudaStream_t st);
+cudaError_t launch_cells_fold(float *cell_grad, float *grads, int64_t tile_params, const GridParams &gp, int n_slots,
+                              int sm_count, cudaStream_t st);
 // lp[i] = FP16(w[i]) (round to nearest even) for i < n: the mixed model's working copy.
 cudaError_t launch_refresh_lp(const float *w, uint16_t *lp, int64_t n, int sm_count, cudaStream_t st);
 

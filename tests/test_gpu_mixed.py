@@ -12,7 +12,8 @@ torch = pytest.importorskip("torch")
 from paper_2507_01631_b300 import build, snk
 from paper_2507_01631_b300.trainer import Trainer, model_from_workload
 from oracle import step as OS
-from gpu_util import GRAD_REL_MIXED, RGB_REL_MIXED, close, make_case, normwise
+from gpu_util import GRAD_REL_MIXED, MAX_FLIPS, RGB_REL_MIXED, close, explain_with_flips, flip_groups, \
+    make_case, mask_flip_deltas, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -46,75 +47,6 @@ def _trainer(ctx, case, seed=5, render=0):
     return tr
 
 
-AMBIGUOUS = 1e-6  # |z| / sum|w x| below which a ReLU decision may go either way in binary32
-
-
-def mask_flip_deltas(case, ref, wc):
-    """Changes of the flat FP64 gradient caused by flipping one ambiguous ReLU
-    decision (a hidden pre-activation within binary32 rounding of zero).  The
-    forward does not move (the unit's activation is ~0 either way); only that
-    sample's backward through the unit does, so each flip is one sample's
-    contribution recomputed with the other mask, and flips in different samples
-    add up."""
-    from oracle import hashgrid, mlp, viewdir
-    cfg = case.cfg
-    smp = ref.smp
-    tiles, cols = OS.unflatten(cfg, wc)
-    lay = cfg.grid()
-    deltas = []
-    for k in range(cfg.n_slots):
-        idx = np.flatnonzero(smp.slot == k)
-        if idx.size == 0:
-            continue
-        col = (cols[0] if cfg.shared_colour else cols[k]) if cfg.colour else None
-        feat = hashgrid.encode(smp.xyz[idx], tiles[k][0], lay)
-        sh = viewdir.sh16(ref.extra["d"][smp.ray[idx]].astype(np.float64)) if (cfg.view_dirs and col is not None) else None
-        _, _, acts = mlp.forward(feat, tiles[k][1], col, sh)
-        layers = [("geo_pre", 0, acts["x0"], tiles[k][1][0]), ("geo_pre", 1, np.maximum(acts["geo_pre"][0], 0), tiles[k][1][1])]
-        if col is not None:
-            layers += [("col_pre", 0, acts.get("col_in", acts["g"]), col[0]),
-                       ("col_pre", 1, np.maximum(acts["col_pre"][0], 0), col[1])]
-        for key, li, h, Wm in layers:
-            z = acts[key][li]
-            ratio = np.abs(z) / (np.abs(h) @ np.abs(Wm).T + 1e-300)
-            for s, j in zip(*np.nonzero(ratio < AMBIGUOUS)):
-                one = {kk: ([a[s:s + 1].copy() for a in v] if isinstance(v, list) else
-                            (v[s:s + 1].copy() if isinstance(v, np.ndarray) else v)) for kk, v in acts.items()}
-                flip = {kk: ([a.copy() for a in v] if isinstance(v, list) else
-                             (v.copy() if isinstance(v, np.ndarray) else v)) for kk, v in one.items()}
-                flip[key][li][0, j] = -flip[key][li][0, j] if flip[key][li][0, j] != 0 else -1e-30
-                ds, dr = ref.dsigma[idx[s]:idx[s] + 1], ref.drgb[idx[s]:idx[s] + 1]
-                g0 = mlp.backward(ds, dr, tiles[k][1], col, one)
-                g1 = mlp.backward(ds, dr, tiles[k][1], col, flip)
-                d = np.zeros(cfg.n_params())
-                dt, dc = OS.unflatten(cfg, d)
-                for q in range(3):
-                    dt[k][1][q] += g1[0][q] - g0[0][q]
-                    if col is not None:
-                        (dc[0] if cfg.shared_colour else dc[k])[q] += g1[1][q] - g0[1][q]
-                dt[k][0][...] += hashgrid.encode_backward(smp.xyz[idx[s]:idx[s] + 1], g1[2] - g0[2], lay)
-                deltas.append(d)
-    return deltas
-
-
-MAX_FLIPS = 8  # accepted flips per step: a binary32 decision flips only within ~1e-7 of zero
-
-
-def explain_with_flips(got, want, deltas):
-    """Greedily add the flip deltas that bring `want` closer to `got`.  Returns the
-    adjusted reference and the norms of the accepted deltas relative to |want|.
-    The reference may move only by exact oracle flips of decisions that are
-    ambiguous in binary32, and by at most MAX_FLIPS of them (asserted by the caller)."""
-    want = want.copy()
-    accepted = []
-    base = max(np.linalg.norm(want), 1e-300)
-    for d in deltas:
-        if np.linalg.norm(got - (want + d)) < np.linalg.norm(got - want):
-            want = want + d
-            accepted.append(float(np.linalg.norm(d) / base))
-    return want, accepted
-
-
 MIXED_CASES = [("tiny_tile", 96, None), ("tiny_window", 160, None), ("tile256_fp32", 512, None),
                ("tile512_full", 512, 48), ("window2x2_full", 512, 48)]
 
@@ -140,7 +72,7 @@ def check_step_against_oracle(case, tr, out):
     m = tr.m.cpu().numpy().astype(np.float64)
     # decisions that may legitimately differ: account for flipped near-zero ReLU masks
     deltas = mask_flip_deltas(case, ref, wc)
-    ref_m, flips = explain_with_flips(m, ref.m, [(1.0 - 0.9) * d for d in deltas])
+    ref_m, flips = explain_with_flips(m, ref.m, [(1.0 - 0.9) * d for d in deltas], flip_groups(case.cfg))
     print("ambiguous ReLU decisions: %d, accepted flips: %d, their sizes relative to |m|: %s"
           % (len(deltas), len(flips), ["%.2e" % f for f in flips]))
     assert len(flips) <= MAX_FLIPS, flips

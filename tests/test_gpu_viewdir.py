@@ -14,7 +14,8 @@ from paper_2507_01631_b300 import build, snk
 from paper_2507_01631_b300.trainer import Trainer, model_from_workload
 from oracle import step as OS
 from gpu_util import GRAD_REL_FP32, GRAD_REL_MIXED, RGB_REL_FP32, RGB_REL_MIXED, close, make_case, normwise
-from test_gpu_mixed import explain_with_flips, mask_flip_deltas, working_copy
+from test_gpu_mixed import working_copy
+from gpu_util import MAX_FLIPS, explain_with_flips, flip_groups, mask_flip_deltas
 
 pytestmark = pytest.mark.gpu
 NAME = "tiny_window_vd"
@@ -67,7 +68,10 @@ def test_train_step_with_view_directions_matches_oracle(ctx, precision, n_rays):
     m = tr.m.cpu().numpy().astype(np.float64)
     ref_m = ref.m
     if mixed:
-        ref_m = explain_with_flips(m, ref.m, [(1.0 - 0.9) * d for d in mask_flip_deltas(case, ref, wc)], None)
+        ref_m, flips = explain_with_flips(m, ref.m, [(1.0 - 0.9) * d for d in mask_flip_deltas(case, ref, wc)],
+                                         flip_groups(case.cfg))
+        print("accepted flips: %d %s" % (len(flips), ["%.2e" % f for f in flips]))
+        assert len(flips) <= MAX_FLIPS, flips
     errs = {}
     for gi, (a, b, mlp_a) in enumerate(OS.group_ranges(case.cfg)):
         if mlp_a > a:
