@@ -178,24 +178,31 @@ def field_forward_work(w, precision, saved=False):
     return mlp_flops_per_sample(w), 12 + 16 + 4 * max(16, w.L * w.F) + vd
 
 
-# DRAM bytes per sample of each kernel measured by ncu on the 32768-ray case of the 512 m tile
-# (tile-local traffic grows with the samples processed), keyed by (precision, kernel, stored
-# activations, forward shape: "split" = dedicated gather warps, "chain" = every thread gathers
-# then runs the chain); a kernel changed since its capture has no entry (traffic null).
-TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per sample of the 32768-ray capture of the 512 m tile x samples per launch"
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_backward", True, ""): 675.6, ("mixed", "field_backward", False, ""): 173.1,
-                            ("mixed", "field_forward", True, "split"): 625.9,
-                            ("mixed", "field_forward", False, "split"): 146.0,
-                            ("mixed", "field_forward", True, "chain"): 626.2,
-                            ("mixed", "field_forward", False, "chain"): 146.0,
-                            ("fp32", "field_backward", False, ""): 736.6, ("fp32", "field_forward", False, ""): 42.5}
+# DRAM bytes per sample (ncu dram__bytes_read.sum + dram__bytes_write.sum over the samples of the
+# launch) of each field kernel, keyed by (precision, kernel, stored activations, forward shape:
+# "split" = dedicated gather warps, "chain" = every thread gathers then runs the chain), with the
+# capture it comes from.  Traffic grows with the samples processed, so a launch's traffic is this
+# figure x its samples.  Only kernels unchanged since their capture have an entry: the others report
+# traffic null.
+WINDOW_CAPTURE = "window2x2_full, 65536 rays (7.98 M samples)"
+TILE_CAPTURE = "tile512_full, 32768 rays (2.86 M samples)"
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_forward", True, "split"): (704.7, WINDOW_CAPTURE),
+                            ("mixed", "field_backward", True, ""): (786.7, WINDOW_CAPTURE),
+                            ("fp32", "field_backward", False, ""): (736.6, TILE_CAPTURE),
+                            ("fp32", "field_forward", False, ""): (42.5, TILE_CAPTURE)}
+
+
+def dram_capture(prec_key, kernel, saved, split):
+    """(measured DRAM bytes per sample, capture) of a field kernel in the given configuration, or
+    None (no capture of that kernel as it stands)."""
+    shape = ("split" if split else "chain") if (kernel == "field_forward" and prec_key == "mixed") else ""
+    return MEASURED_DRAM_PER_SAMPLE.get((prec_key, kernel, bool(saved), shape))
 
 
 def dram_bytes_per_sample(prec_key, kernel, saved, split):
-    """Measured DRAM bytes per sample of a field kernel in the given configuration, or None
-    (no capture of that kernel as it stands)."""
-    shape = ("split" if split else "chain") if (kernel == "field_forward" and prec_key == "mixed") else ""
-    return MEASURED_DRAM_PER_SAMPLE.get((prec_key, kernel, bool(saved), shape))
+    """Measured DRAM bytes per sample of a field kernel in the given configuration, or None."""
+    c = dram_capture(prec_key, kernel, saved, split)
+    return c[0] if c else None
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -414,10 +421,12 @@ def reduction_probe(torch, snk, ctx, n_entries, reps=3):
     return out
 
 
-# L2 reduction sectors per sample of the fused backward (ncu `lts__t_sectors_op_red.sum` over the
-# samples of the launch), keyed by (precision, stored activations); the capture's workload is named
-# beside it.  A kernel changed since its capture has no entry.
-MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (96.9, "tile512_full, 32768 rays")}
+# Table-gradient reductions per sample of the fused backward: ncu lts__t_sectors_srcunit_tex_op_red.sum
+# (each reduction an SM issues, counted once: one 16- or 8-byte reduction is one sector operation;
+# lts__t_sectors_op_red also counts the half of them that cross to the other die's L2 a second time)
+# over the samples of the launch, keyed by (precision, stored activations), with the capture.  The
+# probe's rate is in the same unit.  A kernel changed since its capture has no entry.
+MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (73.7, WINDOW_CAPTURE)}
 
 
 def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=None):
@@ -431,8 +440,11 @@ def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=
                 "traffic": None}
     gbs = method * units / per_launch_s / 1e9
     dram = dram_bytes_per_sample(prec_key, name, saved, split)
+    cap = dram_capture(prec_key, name, saved, split)
     roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / pk["hbm_gbs"], "traffic": dram * units if dram is not None else None,
+            "traffic_source": ("ncu DRAM bytes per sample of the %s capture x samples per launch" % cap[1]) if cap
+            else "no capture of this kernel as it stands",
             "peak_source": "%s hbm_gbs" % pk["source"], "algorithmic_bytes_per_sample": method,
             "units_per_launch": units, "launch_ms": per_launch_s * 1e3}
     design = design_bytes_per_sample(w, prec_key, name, saved)
@@ -457,7 +469,7 @@ def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=
         roof["l2_reduction"] = {"bound": "l2_red", "achieved": sec / 1e9, "peak": pv / 1e9, "unit": "G sectors/s",
                                 "frac": sec / pv, "sectors_per_sample": red[0],
                                 "peak_source": "snk_l2_reduction_probe, 16-byte reductions, measured in this run",
-                                "sectors_source": "ncu lts__t_sectors_op_red.sum per sample, %s" % red[1]}
+                                "sectors_source": "ncu lts__t_sectors_srcunit_tex_op_red.sum per sample, %s" % red[1]}
     return roof
 
 
@@ -626,7 +638,6 @@ def run_ours(args, w):
         roof["step"] = {"algorithmic_bytes_per_sample": step_bytes,
                         "achieved": step_bytes * per_step_samples / step_s / 1e9, "unit": "GB/s",
                         "frac": step_bytes * per_step_samples / step_s / 1e9 / pk["hbm_gbs"]}
-        roof["traffic_source"] = TRAFFIC_SOURCE
         roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
 
     cpu = None

@@ -177,6 +177,35 @@ __device__ __forceinline__ int slot_of(const snk_state *st, int64_t s) {
 
 __device__ __forceinline__ void set_status(snk_state *st, uint32_t bit) { atomicOr(&st->status, bit); }
 
+// ---- L2 residency of the tables and their gradients ---------------------------
+// The FP16 tables the forward gathers from and the binary32 gradients the backward reduces into
+// are re-used by every sample of their slot, while the sample streams (stored activations,
+// features) pass through once: table and gradient accesses carry an evict-last L2 policy, the
+// streams an evict-first one.
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_keep_b32(const void *a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_keep_v2(const void *a, uint64_t pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void red_keep_v4(float *a, float x, float y, float z, float w, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(x), "f"(y), "f"(z),
+               "f"(w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void red_keep_v2(float *a, float x, float y, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(x), "f"(y), "l"(pol) : "memory");
+}
+
 // ---- x-adjacent corner pairs -------------------------------------------------
 // Corners (x, y, z) and (x + 1, y, z) of a cell have entries e0, e1.  When they
 // form one aligned pair {2k, 2k + 1} -- the dense index with x + ... even, or the
@@ -185,46 +214,50 @@ __device__ __forceinline__ void set_status(snk_state *st, uint32_t bit) { atomic
 // The table and gradient blocks start on 16-byte boundaries (level sizes are
 // multiples of 8 entries).
 
-// v0 = table[e0], v1 = table[e1] (FP16 feature pairs).
-__device__ __forceinline__ void load_pair(const __half2 *tab, uint32_t e0, uint32_t e1, __half2 &v0, __half2 &v1) {
+// v0 = table[e0], v1 = table[e1] (FP16 feature pairs), with L2 policy pol.
+__device__ __forceinline__ void load_pair(const __half2 *tab, uint32_t e0, uint32_t e1, __half2 &v0, __half2 &v1,
+                                          uint64_t pol) {
+  uint32_t a, b;
   if ((e0 ^ e1) == 1u) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(tab + (e0 & ~1u)));
-    const uint32_t a = (e0 & 1u) ? u.y : u.x, b = (e0 & 1u) ? u.x : u.y;
-    v0 = *reinterpret_cast<const __half2 *>(&a);
-    v1 = *reinterpret_cast<const __half2 *>(&b);
+    const uint2 u = ld_keep_v2(tab + (e0 & ~1u), pol);
+    a = (e0 & 1u) ? u.y : u.x;
+    b = (e0 & 1u) ? u.x : u.y;
   } else {
-    v0 = __ldg(tab + e0);
-    v1 = __ldg(tab + e1);
+    a = ld_keep_b32(tab + e0, pol);
+    b = ld_keep_b32(tab + e1, pol);
   }
+  v0 = *reinterpret_cast<const __half2 *>(&a);
+  v1 = *reinterpret_cast<const __half2 *>(&b);
 }
 
 // One level of the FP16 hash-grid gather (Sec. 4.1, NGP features): the cell of point x at
 // resolution N (its fractions fr) and the feature pairs of its 8 corners, corner c at
 // (x + (c & 1), y + ((c >> 1) & 1), z + ((c >> 2) & 1)); tab holds the level's entries.
 __device__ __forceinline__ void gather_corners(const __half2 *tab, const float (&x)[3], int N, bool dense,
-                                               uint32_t Tmask, __half2 (&hv)[8], float (&fr)[3]) {
+                                               uint32_t Tmask, __half2 (&hv)[8], float (&fr)[3], uint64_t pol) {
   int ci[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) grid_cell(x[q], N, ci[q], fr[q]);
 #pragma unroll
   for (int c = 0; c < 8; c += 2)
     load_pair(tab, grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask),
-              grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask), hv[c], hv[c + 1]);
+              grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense, Tmask), hv[c], hv[c + 1],
+              pol);
 }
 
 // One dense level from its cell-major FP16 copy (GridParams): the cell of point x at resolution N
 // (its fractions fr) and its 8 corner feature pairs, corner c = dx + 2 dy + 4 dz, in one 32-byte
 // load.  level_cells: the level's first cell (32-byte aligned blocks).
 __device__ __forceinline__ void gather_cell(const uint16_t *level_cells, const float (&x)[3], int N, __half2 (&hv)[8],
-                                            float (&fr)[3]) {
+                                            float (&fr)[3], uint64_t pol) {
   int ci[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) grid_cell(x[q], N, ci[q], fr[q]);
   const uint32_t c = (uint32_t)ci[0] + (uint32_t)N * ((uint32_t)ci[1] + (uint32_t)N * (uint32_t)ci[2]);
   uint32_t r[8];
-  asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "l"(level_cells + 16 * (size_t)c));
+  asm volatile("ld.global.nc.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(level_cells + 16 * (size_t)c), "l"(pol));
 #pragma unroll
   for (int q = 0; q < 8; ++q) hv[q] = *reinterpret_cast<const __half2 *>(&r[q]);
 }
@@ -267,18 +300,16 @@ __device__ __forceinline__ float2 interp_corners(const __half2 (&hv)[8], const f
   return make_float2(f0, f1);
 }
 
-// grad[e0] += w0 * d, grad[e1] += w1 * d (fire-and-forget reductions).
-__device__ __forceinline__ void red_pair(float2 *grad, uint32_t e0, uint32_t e1, float w0, float w1, float2 d) {
+// grad[e0] += w0 * d, grad[e1] += w1 * d (fire-and-forget reductions, L2 policy pol).
+__device__ __forceinline__ void red_pair(float2 *grad, uint32_t e0, uint32_t e1, float w0, float w1, float2 d,
+                                         uint64_t pol) {
   if ((e0 ^ e1) == 1u) {
     const bool odd = e0 & 1u;
     const float a = odd ? w1 : w0, b = odd ? w0 : w1;
-    float *q = reinterpret_cast<float *>(grad + (e0 & ~1u));
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(q), "f"(a * d.x), "f"(a * d.y), "f"(b * d.x),
-                 "f"(b * d.y)
-                 : "memory");
+    red_keep_v4(reinterpret_cast<float *>(grad + (e0 & ~1u)), a * d.x, a * d.y, b * d.x, b * d.y, pol);
   } else {
-    atomicAdd(grad + e0, make_float2(w0 * d.x, w0 * d.y));
-    atomicAdd(grad + e1, make_float2(w1 * d.x, w1 * d.y));
+    red_keep_v2(reinterpret_cast<float *>(grad + e0), w0 * d.x, w0 * d.y, pol);
+    red_keep_v2(reinterpret_cast<float *>(grad + e1), w1 * d.x, w1 * d.y, pol);
   }
 }
 

@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     // level group); they run while the MMA warps work on the next tile ----
     const int s = (t - TT) % TM, lq = (t - TT) / TM;  // sample of the tile, level group
     const int lane = t & 31;                           // a warp: 32 consecutive samples, one level group
+    const uint64_t keep = l2_keep();                   // the gradients stay in L2
     int j = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       if (slot_of(st, r0 + tile * TM) < 0) continue;  // the MMA warps skip the same tiles
@@ -421,10 +422,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
           if (run_sums(v, key, lane) && sv) {
             float *q = a.cell_grad + ((int64_t)ti.slot * gp.n_cells + gp.cell_off[l] + key) * 16;
 #pragma unroll
-            for (int k = 0; k < 16; k += 4)
-              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(q + k), "f"(v[k]), "f"(v[k + 1]),
-                           "f"(v[k + 2]), "f"(v[k + 3])
-                           : "memory");
+            for (int k = 0; k < 16; k += 4) red_keep_v4(q + k, v[k], v[k + 1], v[k + 2], v[k + 3], keep);
           }
         } else if (sv) {
           float2 *gt = gt0 + gp.offset[l];
@@ -436,7 +434,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
             const uint32_t e1 = grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
                                            (uint32_t)gp.T - 1u);
             const float wyz = ((c & 2) ? fr[1] : 1.0f - fr[1]) * ((c & 4) ? fr[2] : 1.0f - fr[2]);
-            red_pair(gt, e0, e1, (1.0f - fr[0]) * wyz, fr[0] * wyz, d);
+            red_pair(gt, e0, e1, (1.0f - fr[0]) * wyz, fr[0] * wyz, d, keep);
           }
         }
       }
@@ -541,6 +539,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       }
     } else if (!BWD) {
       const int s = t & (TM - 1), half = t >> 7;
+      const uint64_t keep = l2_keep();  // the tables stay in L2
       const int64_t sidx = ts + s;
       const bool sval = sidx < slot_end && sidx < r1;
       float xyz[3] = {0.f, 0.f, 0.f};
@@ -561,9 +560,10 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
           fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
           if (l < gp.L && sval) {
             if (a.cells_lp && gp.dense[l])  // one 32-byte load from the cell-major copy
-              gather_cell(a.cells_lp + ((int64_t)slot * gp.n_cells + gp.cell_off[l]) * 16, xyz, gp.res[l], hv[k], fr[k]);
+              gather_cell(a.cells_lp + ((int64_t)slot * gp.n_cells + gp.cell_off[l]) * 16, xyz, gp.res[l], hv[k], fr[k], keep);
             else
-              gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
+              gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k],
+                             keep);
           }
         }
 #pragma unroll
@@ -953,6 +953,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
     // ---- gather warps: tile j's features into buffer j & 1 ----
     const int s = (t - NM) % TM, lq = (t - NM) / TM;  // sample of the tile, level parity
     constexpr int LS = NG / TM;                        // level groups (2)
+    const uint64_t keep = l2_keep();                   // the tables stay in L2
     int j = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const int64_t ts = r0 + tile * TM;
@@ -991,9 +992,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
           fr[k][0] = fr[k][1] = fr[k][2] = 0.f;
           if (l < gp.L && sval) {
             if (a.cells_lp && gp.dense[l])  // one 32-byte load from the cell-major copy
-              gather_cell(a.cells_lp + ((int64_t)slot * gp.n_cells + gp.cell_off[l]) * 16, xyz, gp.res[l], hv[k], fr[k]);
+              gather_cell(a.cells_lp + ((int64_t)slot * gp.n_cells + gp.cell_off[l]) * 16, xyz, gp.res[l], hv[k], fr[k], keep);
             else
-              gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k]);
+              gather_corners(tab0 + gp.offset[l], xyz, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv[k], fr[k],
+                             keep);
           }
         }
 #pragma unroll

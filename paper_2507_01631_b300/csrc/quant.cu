@@ -36,7 +36,7 @@ __global__ void k_gather_amax(const FieldArgs a) {
                              gp.offset[l];
         __half2 hv[8];
         float fr[3];
-        gather_corners(tab, x, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv, fr);
+        gather_corners(tab, x, gp.res[l], gp.dense[l] != 0, (uint32_t)gp.T - 1u, hv, fr, l2_keep());
         const float2 f = interp_corners(hv, fr);
         const float f0 = f.x, f1 = f.y;
         reinterpret_cast<float2 *>(a.feat32)[idx * gp.L + l] = make_float2(f0, f1);

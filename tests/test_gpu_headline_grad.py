@@ -9,7 +9,7 @@ whole images, against the FP64 oracle on the model's FP16 working copy:
 * one tile: the GPU's gradient along directions in the table, the density MLP, the colour MLP
   and its output layer against FP64 central differences of the oracle's loss (the batch's
   samples held fixed), within 5e-3, and the oracle's analytic gradient against the same
-  differences (its own pin at full size): within 1e-6 to 1e-7 along directions whose
+  differences (its own pin at full size): within 1e-6 along directions whose
   differences no ReLU kink spoils, 1e-3 along a random-sign table direction (kink-limited).
 
 Targets: the oracle's rendering of the seeded scene at the batch's pixels, written into
@@ -176,7 +176,7 @@ def test_tile512_full_model_gradients_match_the_oracle_and_central_differences(c
              ("table, random signs", table, rng.standard_normal(mlp_a - a), 1e-7, 1e-3),
              ("density MLP", np.arange(mlp_a, b), rng.standard_normal(b - mlp_a), 1e-8, 2e-6),
              ("colour MLP", np.arange(ca, cb), rng.standard_normal(cb - ca), 1e-8, 2e-6),
-             ("colour output layer", np.arange(v3, cb), rng.standard_normal(cb - v3), 1e-6, 1e-7)]
+             ("colour output layer", np.arange(v3, cb), rng.standard_normal(cb - v3), 1e-6, 1e-6)]
     for nm, idx, vals, step, tol in cases:
         v = np.zeros_like(wc)
         v[idx] = vals

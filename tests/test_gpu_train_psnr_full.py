@@ -11,7 +11,12 @@ batches for both paths).  View 0 is held out: a 256 x 256 grid of its pixels (ev
 column), rendered at bin centres; PSNR over the pixels whose rays the window accepts.
 
 Per path, SEEDS jitter seeds of STEPS steps; the difference of the mean held-out PSNRs must be
-within 0.1 dB (the benchmark metric's condition), its standard error printed beside it."""
+within 0.1 dB (the benchmark metric's condition), its standard error printed beside it.  Both
+paths follow the same learning-rate schedule: I-NGP's constant 1e-2, then over the last
+DECAY_STEPS steps a cosine decay to 1e-4.  At a constant rate the last iterate wanders: held-out
+PSNRs of runs that differ only in the jitter seed spread over 0.3-0.7 dB (measured: 37.0-38.7 dB
+over four seeds), which no affordable number of seeds averages down to a 0.1 dB comparison; the
+decay lets every run settle."""
 import dataclasses
 
 import numpy as np
@@ -27,13 +32,23 @@ from synth import unpack_pixel, workloads as W
 from gpu_util import model_config
 
 pytestmark = pytest.mark.gpu
-STEPS = 600
+STEPS = 800
+DECAY_STEPS = 300
 RAYS = 32768
 POOL = 786432
-SEEDS = [41, 42, 43, 44]
+SEEDS = [41, 42, 43, 44, 45]
 
 
-def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr_at_full_model_size():
+def lr_at(i, steps=STEPS, decay=DECAY_STEPS, lr0=1e-2, lr1=1e-4):
+    """Learning rate of step i: lr0, then a cosine from lr0 to lr1 over the last `decay` steps."""
+    k = i - (steps - decay)
+    if decay <= 0 or k < 0:
+        return lr0
+    return lr1 + 0.5 * (lr0 - lr1) * (1.0 + np.cos(np.pi * (k + 1) / decay))
+
+
+def equal_psnr_study(steps=STEPS, seeds=SEEDS, decay=DECAY_STEPS):
+    """Held-out PSNR of the untrained model and, per path, of each seed's trained model."""
     build.build()
     assert torch.cuda.is_available()
     w = dataclasses.replace(W.get("window2x2_full"), n_rays=RAYS)
@@ -54,7 +69,7 @@ def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr_at_full_model_size():
         img[r[m] - cam.crop[0], c[m] - cam.crop[1]] = col[m]
         crops.append(torch.from_numpy(img).cuda())
     rng = np.random.default_rng(7)
-    batches = torch.from_numpy(pool[rng.integers(0, POOL, (STEPS, RAYS))].view(np.int32)).cuda()
+    batches = torch.from_numpy(pool[rng.integers(0, POOL, (steps, RAYS))].view(np.int32)).cuda()
     # held-out view 0
     c0 = cams[0]
     rr, cc = np.meshgrid(np.arange(4, c0.height, 8), np.arange(4, c0.width, 8), indexing="ij")
@@ -82,15 +97,21 @@ def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr_at_full_model_size():
     for name, prec in (("fp32", snk.SNK_FP32), ("mixed", snk.SNK_MIXED)):
         model = model_from_workload(w, prec)
         vals = []
-        for seed in SEEDS:
+        for seed in seeds:
             tr = Trainer(ctx, model, win, snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, seed, 0), params)
-            for i in range(STEPS):
+            for i in range(steps):
+                tr.adam = snk.adam_struct(lr=lr_at(i, steps, decay))
                 tr.train_step(batches[i])
             assert ctx.sync_status(tr.state) == snk.SNK_OK
             vals.append(held_out_psnr(tr))
             del tr
         psnr[name] = np.array(vals)
     ctx.close()
+    return psnr0, psnr
+
+
+def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr_at_full_model_size():
+    psnr0, psnr = equal_psnr_study()
     d = psnr["mixed"] - psnr["fp32"]
     delta = float(d.mean())
     se = float(d.std(ddof=1) / np.sqrt(len(d)))
