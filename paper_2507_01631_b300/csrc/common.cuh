@@ -313,6 +313,21 @@ __device__ __forceinline__ void red_pair(float2 *grad, uint32_t e0, uint32_t e1,
   }
 }
 
+// grad[e0] += a, grad[e1] += b (already weighted sums), merged when the two share an aligned pair.
+__device__ __forceinline__ void red_pair_sums(float2 *grad, uint32_t e0, uint32_t e1, float2 a, float2 b,
+                                              uint64_t pol) {
+  if ((e0 ^ e1) == 1u) {
+    float *q = reinterpret_cast<float *>(grad + (e0 & ~1u));
+    if (e0 & 1u)
+      red_keep_v4(q, b.x, b.y, a.x, a.y, pol);
+    else
+      red_keep_v4(q, a.x, a.y, b.x, b.y, pol);
+  } else {
+    red_keep_v2(reinterpret_cast<float *>(grad + e0), a.x, a.y, pol);
+    red_keep_v2(reinterpret_cast<float *>(grad + e1), b.x, b.y, pol);
+  }
+}
+
 // ---- E4M3 (OCP 8-bit float: sign, 4 exponent bits with bias 7, 3 mantissa bits,
 // largest finite 448, no infinities) -----------------------------------------
 // Two binary32 values to an E4M3 pair (lo in the low byte): round to nearest

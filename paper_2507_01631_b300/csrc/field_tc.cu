@@ -57,6 +57,15 @@ constexpr int TT = 256;  // threads of the MMA / epilogue warps (warps 0-7)
 // enough that the scatter binds, and a second thread per sample shortens it.
 __host__ __device__ constexpr int scatter_threads(bool sv) { return sv ? 256 : 128; }
 constexpr uint32_t kChainBar = 1;  // named barrier of the 256 MMA / epilogue threads
+// Backward: thread 0 issues each layer's input-gradient MMAs (the chain waits for them before the
+// layer's epilogue); this thread issues the layer's weight-gradient MMAs into their own mbarrier,
+// waited one layer later.  Issuing a tcgen05.mma takes tens of cycles whatever its N, so the weight
+// gradients (8 of a layer's up to 16 MMAs) would otherwise lengthen every round of the chain.
+constexpr int kWIssuer = 32;
+// Scatter: levels up to this resolution (cells of 3.3 m and more on a 512 m tile) sum the terms of
+// a warp's samples that share a cell before reducing; finer levels rarely share one (28-32
+// distinct cells per 32 consecutive samples at N >= 153), where the shuffles would not pay.
+constexpr int kRunMaxN = 160;
 // Split FP16 operands (Markidis et al. 2018): every activation and delta x
 // that feeds an MMA is carried as hi = fp16(x) and lo = fp16((x - hi) * 2^11);
 // a layer runs two MMAs, hi * W and lo * W, into separate tensor-memory
@@ -132,28 +141,40 @@ __device__ __forceinline__ float2 unpack_h2(uint32_t u) {
   return __half22float2(v);
 }
 
+// The MMA helpers below are issued by one thread, one tcgen05.mma per K step of 16: each builds
+// its two shared-memory descriptors once and steps them by adding the K step's byte offset / 16 to
+// the address field (the addresses stay below 2^18, so the 14-bit field never carries), and all
+// sizes are compile-time constants, so the issuing thread spends a few instructions per MMA instead
+// of rebuilding both descriptors.
+
 // D[128 x N] = A[128 x K] * B^T, A K-major (128 rows), B = weights [N x K] K-major (N rows).
-__device__ __forceinline__ void mma_fwd(uint32_t d, uint32_t a, uint32_t b, int K, int N) {
-  const uint32_t id = tc::idesc_f16(TM, N, 0, 0);
+template <int K, int N>
+__device__ __forceinline__ void mma_fwd(uint32_t d, uint32_t a, uint32_t b) {
+  constexpr uint32_t id = tc::idesc_f16(TM, N, 0, 0);
+  const uint64_t da = tc::desc(a, (TM / 8) * 128, 128), db = tc::desc(b, (N / 8) * 128, 128);
+#pragma unroll
   for (int j = 0; j < K / 16; ++j)
-    tc::mma_f16(d, tc::desc(a + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                 tc::desc(b + j * 2 * (N / 8) * 128, (N / 8) * 128, 128), id, j > 0);
+    tc::mma_f16(d, da + (uint64_t)(j * 2 * (TM / 8) * 8), db + (uint64_t)(j * 2 * (N / 8) * 8), id, j > 0);
 }
 
 // D[128 x N] = delta[128 x K] * W, delta K-major, W stored [K rows x N] and read MN-major.
-__device__ __forceinline__ void mma_dx(uint32_t d, uint32_t delta, uint32_t w, int K, int N) {
-  const uint32_t id = tc::idesc_f16(TM, N, 0, 1);
+template <int K, int N>
+__device__ __forceinline__ void mma_dx(uint32_t d, uint32_t delta, uint32_t w) {
+  constexpr uint32_t id = tc::idesc_f16(TM, N, 0, 1);
+  const uint64_t da = tc::desc(delta, (TM / 8) * 128, 128), db = tc::desc(w, 128, (K / 8) * 128);
+#pragma unroll
   for (int j = 0; j < K / 16; ++j)
-    tc::mma_f16(d, tc::desc(delta + j * 2 * (TM / 8) * 128, (TM / 8) * 128, 128),
-                 tc::desc(w + j * 2 * 128, 128, (K / 8) * 128), id, j > 0);
+    tc::mma_f16(d, da + (uint64_t)(j * 2 * (TM / 8) * 8), db + (uint64_t)(j * 16), id, j > 0);
 }
 
 // D[128 (rows = output units, padded) x N] (+)= delta^T * X over the 128 samples; both read MN-major.
-__device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, int N, uint32_t accumulate) {
-  const uint32_t id = tc::idesc_f16(TM, N, 1, 1);
+template <int N>
+__device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, uint32_t accumulate) {
+  constexpr uint32_t id = tc::idesc_f16(TM, N, 1, 1);
+  const uint64_t da = tc::desc(delta, 128, (TM / 8) * 128), db = tc::desc(x, 128, (TM / 8) * 128);
+#pragma unroll
   for (int j = 0; j < TM / 16; ++j)
-    tc::mma_f16(d, tc::desc(delta + j * 2 * 128, 128, (TM / 8) * 128), tc::desc(x + j * 2 * 128, 128, (TM / 8) * 128),
-                 id, (j > 0) || accumulate);
+    tc::mma_f16(d, da + (uint64_t)(j * 16), db + (uint64_t)(j * 16), id, (j > 0) || accumulate);
 }
 
 // Copy a row-major [rows x cols] 16-bit matrix from global into the core layout (R = rpad rows,
@@ -278,6 +299,9 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   TileInfo *info = reinterpret_cast<TileInfo *>(sm + Y::MISC + 48);  // [2]
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Y::MISC + 80);
   uint64_t *abar = reinterpret_cast<uint64_t *>(sm + Y::MISC + 88);  // stored activations landed
+  // weight-gradient MMAs completed: commit i (counted over the kernel) arrives on wbar[i & 1], so
+  // neither barrier runs more than one phase ahead of the threads that wait for it
+  uint64_t *wbar = reinterpret_cast<uint64_t *>(sm + Y::MISC + 96);  // [2]
   float *dfbuf = reinterpret_cast<float *>(sm + Y::DF);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int r = 32 * (warp & 3) + lane;  // TMEM lane = tile row of this thread
@@ -298,6 +322,10 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     }
     *abort_flag = 0;
     if (SV) tc::mbar_init(abar, 1);
+    if (BWD) {
+      tc::mbar_init(wbar, 1);
+      tc::mbar_init(wbar + 1, 1);
+    }
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, Y::TCOLS);
@@ -309,6 +337,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   const uint32_t tmem = *tslot;
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   uint32_t phase = 0, aphase = 0;
+  // weight-gradient commits issued and waited for (every MMA / epilogue thread counts them alike)
+  uint32_t w_issued = 0, w_waited = 0;
   bool abort = false, a_pending = false;
 
   int64_t r0 = 0, r1 = st->slot_base[kMaxSlots];
@@ -325,6 +355,21 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   auto sync_mma = [&]() -> bool {
     const bool ok = tc::mbar_wait(mbar, phase);
     if (ok) phase ^= 1u;
+    tc::fence_after_sync();
+    return !tc::bar_or(kChainBar, TT, !ok);
+  };
+  // backward layer: wait for this layer's input-gradient MMAs and, with wait_w, for the previous
+  // layer's weight-gradient MMAs (whose operands the next epilogues may overwrite); uniform result
+  auto wait_w_next = [&]() -> bool {  // the oldest weight-gradient commit not yet waited for
+    const bool ok = tc::mbar_wait(wbar + (w_waited & 1u), (w_waited >> 1) & 1u);
+    if (ok) ++w_waited;
+    return ok;
+  };
+  auto sync_mma_w = [&](bool wait_w) -> bool {
+    ++w_issued;  // this layer's weight-gradient commit
+    bool ok = tc::mbar_wait(mbar, phase);
+    if (ok) phase ^= 1u;
+    if (wait_w) ok = wait_w_next() && ok;
     tc::fence_after_sync();
     return !tc::bar_or(kChainBar, TT, !ok);
   };
@@ -423,6 +468,31 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
             float *q = a.cell_grad + ((int64_t)ti.slot * gp.n_cells + gp.cell_off[l] + key) * 16;
 #pragma unroll
             for (int k = 0; k < 16; k += 4) red_keep_v4(q + k, v[k], v[k + 1], v[k + 2], v[k + 3], keep);
+          }
+        } else if (N <= kRunMaxN) {
+          // coarse hashed level (cells of a few metres): the same run sums, then the run's last
+          // lane adds the 8 corner sums through the hash, x-adjacent pairs merged as below
+          const uint32_t key = sv ? (uint32_t)ci[0] + (uint32_t)N * ((uint32_t)ci[1] + (uint32_t)N * (uint32_t)ci[2])
+                                  : 0xffffffffu;
+          float v[16];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float wc = ((c & 1) ? fr[0] : 1.0f - fr[0]) * ((c & 2) ? fr[1] : 1.0f - fr[1]) *
+                             ((c & 4) ? fr[2] : 1.0f - fr[2]);
+            v[2 * c] = wc * d.x;
+            v[2 * c + 1] = wc * d.y;
+          }
+          if (run_sums(v, key, lane) && sv) {
+            float2 *gt = gt0 + gp.offset[l];
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) {
+              const uint32_t e0 = grid_index(ci[0], ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                             (uint32_t)gp.T - 1u);
+              const uint32_t e1 = grid_index(ci[0] + 1, ci[1] + ((c >> 1) & 1), ci[2] + ((c >> 2) & 1), N, dense,
+                                             (uint32_t)gp.T - 1u);
+              red_pair_sums(gt, e0, e1, make_float2(v[2 * c], v[2 * c + 1]), make_float2(v[2 * c + 2], v[2 * c + 3]),
+                            keep);
+            }
           }
         } else if (sv) {
           float2 *gt = gt0 + gp.offset[l];
@@ -627,8 +697,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 
     // ---- forward MLP ----
     if (t == 0) {
-      mma_fwd(tmem, s0 + Y::X0, s0 + Y::W1, INP, 64);
-      if (!Q8) mma_fwd(tmem + Y::C_DL, s0 + Y::XL0, s0 + Y::W1, INP, 64);
+      mma_fwd<INP, 64>(tmem, s0 + Y::X0, s0 + Y::W1);
+      if (!Q8) mma_fwd<INP, 64>(tmem + Y::C_DL, s0 + Y::XL0, s0 + Y::W1);
       tc::commit(mbar);
     }
     abort = !sync_mma();
@@ -639,8 +709,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       epi64<0>(trow, trow + Y::C_DL, sm + Y::X1, sm + Y::XLA, nullptr, r, ch, 1.0f, gact ? gact + Y::A1 : nullptr);
     handoff();
     if (t == 0) {
-      mma_fwd(tmem, s0 + Y::X1, s0 + Y::W2, 64, 64);
-      mma_fwd(tmem + Y::C_DL, s0 + Y::XLA, s0 + Y::W2, 64, 64);
+      mma_fwd<64, 64>(tmem, s0 + Y::X1, s0 + Y::W2);
+      mma_fwd<64, 64>(tmem + Y::C_DL, s0 + Y::XLA, s0 + Y::W2);
       tc::commit(mbar);
     }
     abort = !sync_mma();
@@ -648,8 +718,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     epi64<0>(trow, trow + Y::C_DL, sm + Y::X2, sm + Y::XLB, nullptr, r, ch, 1.0f, gact ? gact + Y::A2 : nullptr);
     handoff();
     if (t == 0) {
-      mma_fwd(tmem, s0 + Y::X2, s0 + Y::W3, 64, 16);
-      mma_fwd(tmem + Y::C_DL, s0 + Y::XLB, s0 + Y::W3, 64, 16);
+      mma_fwd<64, 16>(tmem, s0 + Y::X2, s0 + Y::W3);
+      mma_fwd<64, 16>(tmem + Y::C_DL, s0 + Y::XLB, s0 + Y::W3);
       tc::commit(mbar);
     }
     abort = !sync_mma();
@@ -675,8 +745,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     handoff();
     if (COL) {
       if (t == 0) {
-        mma_fwd(tmem, s0 + Y::X3, s0 + Y::V1, CIN, 64);
-        mma_fwd(tmem + Y::C_DL, s0 + Y::XL3, s0 + Y::V1, CIN, 64);
+        mma_fwd<CIN, 64>(tmem, s0 + Y::X3, s0 + Y::V1);
+        mma_fwd<CIN, 64>(tmem + Y::C_DL, s0 + Y::XL3, s0 + Y::V1);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -684,8 +754,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       epi64<0>(trow, trow + Y::C_DL, sm + Y::X4, sm + Y::XLA, nullptr, r, ch, 1.0f, gact ? gact + Y::A4 : nullptr);
       handoff();
       if (t == 0) {
-        mma_fwd(tmem, s0 + Y::X4, s0 + Y::V2, 64, 64);
-        mma_fwd(tmem + Y::C_DL, s0 + Y::XLA, s0 + Y::V2, 64, 64);
+        mma_fwd<64, 64>(tmem, s0 + Y::X4, s0 + Y::V2);
+        mma_fwd<64, 64>(tmem + Y::C_DL, s0 + Y::XLA, s0 + Y::V2);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -693,8 +763,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       epi64<0>(trow, trow + Y::C_DL, sm + Y::X5, sm + Y::XLB, nullptr, r, ch, 1.0f, gact ? gact + Y::A5 : nullptr);
       handoff();
       if (t == 0) {
-        mma_fwd(tmem, s0 + Y::X5, s0 + Y::V3, 64, 16);
-        mma_fwd(tmem + Y::C_DL, s0 + Y::XLB, s0 + Y::V3, 64, 16);
+        mma_fwd<64, 16>(tmem, s0 + Y::X5, s0 + Y::V3);
+        mma_fwd<64, 16>(tmem + Y::C_DL, s0 + Y::XLB, s0 + Y::V3);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -745,34 +815,43 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     if (COL) {
       // dc2 = delta3 * V3, dV3 += delta3^T c2
       if (t == 0) {
-        mma_dx(tmem, s0 + Y::D3, s0 + Y::V3, 16, 64);
-        mma_dx(tmem + Y::C_DL, s0 + Y::D3L, s0 + Y::V3, 16, 64);
-        mma_dw(tmem + Y::C_V3, s0 + Y::D3, s0 + Y::X5, 64, acc);
+        mma_dx<16, 64>(tmem, s0 + Y::D3, s0 + Y::V3);
+        mma_dx<16, 64>(tmem + Y::C_DL, s0 + Y::D3L, s0 + Y::V3);
         tc::commit(mbar);
       }
-      abort = !sync_mma();
+      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued) (commit index w_issued)
+        mma_dw<64>(tmem + Y::C_V3, s0 + Y::D3, s0 + Y::X5, acc);
+        tc::commit(wbar + (w_issued & 1u));
+      }
+      abort = !sync_mma_w(false);
       if (abort) break;
       epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X5, r, ch);
       handoff();
       // dc1 = delta_c2 * V2, dV2 += delta_c2^T c1
       if (t == 0) {
-        mma_dx(tmem, s0 + Y::DA, s0 + Y::V2, 64, 64);
-        mma_dx(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::V2, 64, 64);
-        mma_dw(tmem + Y::C_V2, s0 + Y::DA, s0 + Y::X4, 64, acc);
+        mma_dx<64, 64>(tmem, s0 + Y::DA, s0 + Y::V2);
+        mma_dx<64, 64>(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::V2);
         tc::commit(mbar);
       }
-      abort = !sync_mma();
+      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued) (commit index w_issued)
+        mma_dw<64>(tmem + Y::C_V2, s0 + Y::DA, s0 + Y::X4, acc);
+        tc::commit(wbar + (w_issued & 1u));
+      }
+      abort = !sync_mma_w(true);
       if (abort) break;
       epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X4, r, ch);
       handoff();
       // dg = delta_c1 * V1 (+ dsigma term; N = 16: the g columns of V1), dV1 += delta_c1^T [g | SH]
       if (t == 0) {
-        mma_dx(tmem, s0 + Y::DB, s0 + Y::V1, 64, 16);
-        mma_dx(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::V1, 64, 16);
-        mma_dw(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, CIN, acc);
+        mma_dx<64, 16>(tmem, s0 + Y::DB, s0 + Y::V1);
+        mma_dx<64, 16>(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::V1);
         tc::commit(mbar);
       }
-      abort = !sync_mma();
+      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued) (commit index w_issued)
+        mma_dw<CIN>(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, acc);
+        tc::commit(wbar + (w_issued & 1u));
+      }
+      abort = !sync_mma_w(true);
       if (abort) break;
       if (ch == 0) {
         float dg[16];
@@ -787,36 +866,45 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       }
       handoff();
     }
-    // dh2 = delta_g * W3 (masked by h2), dW3 += delta_g^T h2
+    // dh2 = delta_g * W3 (masked by h2), dW3 += delta_g^T h2 (the first layer without a colour net)
     if (t == 0) {
-      mma_dx(tmem, s0 + Y::DG, s0 + Y::W3, 16, 64);
-      mma_dx(tmem + Y::C_DL, s0 + Y::DGL, s0 + Y::W3, 16, 64);
-      mma_dw(tmem + Y::C_W3, s0 + Y::DG, s0 + Y::X2, 64, acc);
+      mma_dx<16, 64>(tmem, s0 + Y::DG, s0 + Y::W3);
+      mma_dx<16, 64>(tmem + Y::C_DL, s0 + Y::DGL, s0 + Y::W3);
       tc::commit(mbar);
     }
-    abort = !sync_mma();
+    if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
+      mma_dw<64>(tmem + Y::C_W3, s0 + Y::DG, s0 + Y::X2, acc);
+      tc::commit(wbar + (w_issued & 1u));
+    }
+    abort = !sync_mma_w(COL);
     if (abort) break;
     epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X2, r, ch);
     handoff();
     // dh1 = delta_h2 * W2 (masked by h1), dW2 += delta_h2^T h1
     if (t == 0) {
-      mma_dx(tmem, s0 + Y::DA, s0 + Y::W2, 64, 64);
-      mma_dx(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::W2, 64, 64);
-      mma_dw(tmem + Y::C_W2, s0 + Y::DA, s0 + Y::X1, 64, acc);
+      mma_dx<64, 64>(tmem, s0 + Y::DA, s0 + Y::W2);
+      mma_dx<64, 64>(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::W2);
       tc::commit(mbar);
     }
-    abort = !sync_mma();
+    if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
+      mma_dw<64>(tmem + Y::C_W2, s0 + Y::DA, s0 + Y::X1, acc);
+      tc::commit(wbar + (w_issued & 1u));
+    }
+    abort = !sync_mma_w(true);
     if (abort) break;
     epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X1, r, ch);
     handoff();
     // dfeat = delta_h1 * W1, dW1 += delta_h1^T feat
     if (t == 0) {
-      mma_dx(tmem, s0 + Y::DB, s0 + Y::W1, 64, INP);
-      mma_dx(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::W1, 64, INP);
-      mma_dw(tmem + Y::C_W1, s0 + Y::DB, s0 + Y::X0, INP, acc);
+      mma_dx<64, INP>(tmem, s0 + Y::DB, s0 + Y::W1);
+      mma_dx<64, INP>(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::W1);
       tc::commit(mbar);
     }
-    abort = !sync_mma();
+    if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
+      mma_dw<INP>(tmem + Y::C_W1, s0 + Y::DB, s0 + Y::X0, acc);
+      tc::commit(wbar + (w_issued & 1u));
+    }
+    abort = !sync_mma_w(true);
     if (abort) break;
     fresh = false;
     // ---- hand dfeat (D_hi + 2^-11 D_lo, binary32) to the scatter warps through DF[b] ----
@@ -824,7 +912,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     int drained = 0;
     if (t == 0 && jt >= 2) drained = tc::mbar_wait_or_abort(empty + b, ((jt >> 1) - 1) & 1, abort_flag);
     if (t == 0 && drained == 2) atomicOr(&st_rw->status, kStatusTimeout);
-    abort = tc::bar_or(kChainBar, TT, drained != 0);
+    // the last layer's weight gradients: their operands (X0, the last delta) are rewritten by the
+    // next tile
+    bool okw = true;
+    while (okw && w_waited != w_issued) okw = wait_w_next();
+    tc::fence_after_sync();
+    abort = tc::bar_or(kChainBar, TT, drained != 0 || !okw);
     if (abort) break;
     const int c0 = ch * 16;
     if (c0 < IN) {
@@ -856,6 +949,9 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     if (t == 0) atomicOr(&st_rw->status, kStatusTimeout);
     *abort_flag = 1;             // releases scatter warps waiting for a tile
     tc::mbar_wait(mbar, phase);  // bounded: let any MMA still in flight finish before freeing TMEM
+    // bounded: weight-gradient MMAs still in flight (one phase per commit, waited in order)
+    while (BWD && w_waited != w_issued && wait_w_next()) {
+    }
     // bounded: bulk copies still writing this CTA's shared memory land before it exits
     if (SV && a_pending) tc::mbar_wait(abar, aphase);
   } else if (BWD && cur_slot >= 0) {
@@ -1075,8 +1171,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
       }
       const uint32_t fh = s0 + Y::FB + b * Y::FBS, fl = fh + TM * INP * 2;
       if (t == 0) {
-        mma_fwd(tmem, fh, s0 + Y::W1, INP, 64);
-        mma_fwd(tmem + Y::C_DL, fl, s0 + Y::W1, INP, 64);
+        mma_fwd<INP, 64>(tmem, fh, s0 + Y::W1);
+        mma_fwd<INP, 64>(tmem + Y::C_DL, fl, s0 + Y::W1);
         tc::commit(mbar);
         tc::commit(empty + b);
       }
@@ -1087,8 +1183,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
         epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A1 : nullptr);
       handoff();
       if (t == 0) {
-        mma_fwd(tmem, s0 + Y::X, s0 + Y::W2, 64, 64);
-        mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W2, 64, 64);
+        mma_fwd<64, 64>(tmem, s0 + Y::X, s0 + Y::W2);
+        mma_fwd<64, 64>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W2);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -1097,8 +1193,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
         epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A2 : nullptr);
       handoff();
       if (t == 0) {
-        mma_fwd(tmem, s0 + Y::X, s0 + Y::W3, 64, 16);
-        mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W3, 64, 16);
+        mma_fwd<64, 16>(tmem, s0 + Y::X, s0 + Y::W3);
+        mma_fwd<64, 16>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W3);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -1125,8 +1221,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
       handoff();
       if (COL) {
         if (t == 0) {
-          mma_fwd(tmem, s0 + Y::X, s0 + Y::V1, CIN, 64);
-          mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V1, CIN, 64);
+          mma_fwd<CIN, 64>(tmem, s0 + Y::X, s0 + Y::V1);
+          mma_fwd<CIN, 64>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V1);
           tc::commit(mbar);
         }
         abort = !sync_mma();
@@ -1135,8 +1231,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
         epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A4 : nullptr);
         handoff();
         if (t == 0) {
-          mma_fwd(tmem, s0 + Y::X, s0 + Y::V2, 64, 64);
-          mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V2, 64, 64);
+          mma_fwd<64, 64>(tmem, s0 + Y::X, s0 + Y::V2);
+          mma_fwd<64, 64>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V2);
           tc::commit(mbar);
         }
         abort = !sync_mma();
@@ -1145,8 +1241,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
         epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A5 : nullptr);
         handoff();
         if (t == 0) {
-          mma_fwd(tmem, s0 + Y::X, s0 + Y::V3, 64, 16);
-          mma_fwd(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V3, 64, 16);
+          mma_fwd<64, 16>(tmem, s0 + Y::X, s0 + Y::V3);
+          mma_fwd<64, 16>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V3);
           tc::commit(mbar);
         }
         abort = !sync_mma();
