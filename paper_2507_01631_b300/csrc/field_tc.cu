@@ -536,6 +536,13 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     const int64_t slot_end = (int64_t)st->slot_base[slot] + st->slot_count[slot];
     const int64_t idx = ts + r;
     const bool valid = idx < slot_end && idx < r1;
+    // backward: this row's upstream gradient and (with stored activations) forward outputs, loaded
+    // now so that their latency passes while the tile's operands arrive
+    float4 up = make_float4(0.f, 0.f, 0.f, 0.f), fo = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (BWD && ch == 0 && valid) {
+      up = reinterpret_cast<const float4 *>(a.dsr)[idx];
+      if (SV) fo = reinterpret_cast<const float4 *>(a.sigma_rgb)[idx];
+    }
     uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);  // [hi | lo] of the tile
     // this tile's stored activations: written by a training forward, read back by the backward
     uint8_t *gact = a.acts ? reinterpret_cast<uint8_t *>(a.acts) + (ts / TM) * (int64_t)ACT : nullptr;
@@ -686,12 +693,10 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       abort = tc::bar_or(kChainBar, TT, !ok);
       if (abort) break;
       if (ch == 0) {
-        float4 sr = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) sr = reinterpret_cast<const float4 *>(a.sigma_rgb)[idx];
-        e0 = fminf(fmaxf(sr.x, __expf(-15.f)), __expf(15.f));
-        rgb[0] = sr.y;
-        rgb[1] = sr.z;
-        rgb[2] = sr.w;
+        e0 = fminf(fmaxf(fo.x, __expf(-15.f)), __expf(15.f));
+        rgb[0] = fo.y;
+        rgb[1] = fo.z;
+        rgb[2] = fo.w;
       }
     } else {
 
@@ -791,8 +796,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     // ---- backward ----
     // output deltas (the upstream gradient already carries the loss scale)
     if (ch == 0) {
-      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) d = reinterpret_cast<const float4 *>(a.dsr)[idx];
+      const float4 d = up;
       const float dg0 = d.x * e0;
       const float d3[3] = {d.y * rgb[0] * (1.f - rgb[0]), d.z * rgb[1] * (1.f - rgb[1]), d.w * rgb[2] * (1.f - rgb[2])};
       float row[16];
