@@ -31,7 +31,19 @@ RAYS = 4096
 SEEDS = list(range(20, 36))
 
 
-def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr():
+DECAY_STEPS = 0  # constant learning rate (the full-size study decays it over its last steps)
+
+
+def lr_at(i, steps, decay, lr0=1e-2, lr1=1e-4):
+    """lr0, then a cosine from lr0 to lr1 over the last `decay` steps (none for decay = 0)."""
+    k = i - (steps - decay)
+    if decay <= 0 or k < 0:
+        return lr0
+    return lr1 + 0.5 * (lr0 - lr1) * (1.0 + np.cos(np.pi * (k + 1) / decay))
+
+
+def equal_psnr_study(steps=STEPS, seeds=SEEDS, decay=DECAY_STEPS):
+    """Held-out PSNR of each seed's trained model, per path."""
     build.build()
     assert torch.cuda.is_available()
     w = dataclasses.replace(W.get("tiny_window"), n_views=6, n_rays=RAYS)
@@ -41,7 +53,7 @@ def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr():
     lay = cfg.grid()
     params = W.init_params(lay.n_params, cfg.geo_shapes(), cfg.col_shapes(), cfg.n_slots, cfg.n_colour_blocks(), 3)
     batches = [torch.from_numpy(synth.random_pixels(1000 + i, RAYS, cams, views=np.arange(1, 6)).view(np.int32)).cuda()
-               for i in range(STEPS)]
+               for i in range(steps)]
     c0 = cams[0]
     rr, cc = np.meshgrid(np.arange(c0.crop[2]), np.arange(c0.crop[3]), indexing="ij")
     held = synth.pack_pixel(np.zeros(rr.size, int), rr.ravel() + c0.crop[0], cc.ravel() + c0.crop[1])
@@ -54,10 +66,11 @@ def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr():
     for name, prec in (("fp32", snk.SNK_FP32), ("mixed", snk.SNK_MIXED)):
         model = model_from_workload(w, prec)
         vals = []
-        for seed in SEEDS:
+        for seed in seeds:
             tr = Trainer(ctx, model, snk.window_struct(w.window()),
                          snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 0, seed, 0), params)
-            for b in batches:
+            for i, b in enumerate(batches):
+                tr.adam = snk.adam_struct(lr=lr_at(i, steps, decay))
                 tr.train_step(b)
             assert ctx.sync_status(tr.state) == snk.SNK_OK
             tr.sampler = snk.sampler_struct(w.K_ray, w.K_min, w.K_max, 1, 0, 0)
@@ -67,6 +80,11 @@ def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr():
             vals.append(float(-10.0 * np.log10(np.mean((rgb - gt) ** 2))))
         psnr[name] = np.array(vals)
     ctx.close()
+    return psnr
+
+
+def test_fp32_per_tile_and_mixed_batched_reach_equal_psnr():
+    psnr = equal_psnr_study()
     d = psnr["mixed"] - psnr["fp32"]
     delta = float(d.mean())
     se = float(d.std(ddof=1) / np.sqrt(len(d)))
