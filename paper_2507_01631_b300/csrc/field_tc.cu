@@ -118,9 +118,10 @@ struct L {
   static constexpr int DFS = IN + 4;
   static constexpr int DF = END;
   static constexpr int DF_BYTES = BWD ? 2 * TM * DFS * 4 : 0;
-  // mbarriers (MMA commit, ring full[2] / empty[2]), TMEM address, tile info[2], abort flag
+  // mbarriers (MMA commit, ring full[2] / empty[2]), TMEM address, tile info[2], abort flag,
+  // weight-gradient commits [2], stored activations landed [6]
   static constexpr int MISC = DF + DF_BYTES;
-  static constexpr int SMEM = MISC + 128;
+  static constexpr int SMEM = MISC + 192;
   static constexpr uint32_t TCOLS = BWD ? 512 : 128;
   // tensor-memory columns: 0..63 accumulator of the high parts; C_DL the low parts
   static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
@@ -298,7 +299,10 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Y::MISC + 40);
   TileInfo *info = reinterpret_cast<TileInfo *>(sm + Y::MISC + 48);  // [2]
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Y::MISC + 80);
-  uint64_t *abar = reinterpret_cast<uint64_t *>(sm + Y::MISC + 88);  // stored activations landed
+  // stored activations landed, one barrier a buffer, numbered in the order the backward reads
+  // them: c2, c1, g (with a colour network), h2, h1, the features
+  uint64_t *abar = reinterpret_cast<uint64_t *>(sm + Y::MISC + 128);  // [6]
+  constexpr int kGX2 = COL ? 3 : 0, kGX1 = kGX2 + 1, kGX0 = kGX2 + 2;
   // weight-gradient MMAs completed: commit i (counted over the kernel) arrives on wbar[i & 1], so
   // neither barrier runs more than one phase ahead of the threads that wait for it
   uint64_t *wbar = reinterpret_cast<uint64_t *>(sm + Y::MISC + 96);  // [2]
@@ -321,7 +325,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       }
     }
     *abort_flag = 0;
-    if (SV) tc::mbar_init(abar, 1);
+    if (SV)
+      for (int i = 0; i <= kGX0; ++i) tc::mbar_init(abar + i, 1);
     if (BWD) {
       tc::mbar_init(wbar, 1);
       tc::mbar_init(wbar + 1, 1);
@@ -339,7 +344,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   uint32_t phase = 0, aphase = 0;
   // weight-gradient commits issued and waited for (every MMA / epilogue thread counts them alike)
   uint32_t w_issued = 0, w_waited = 0;
-  bool abort = false, a_pending = false;
+  bool abort = false;
+  uint32_t a_pend = 0;  // thread 0: stored-activation copies issued and not yet waited for
 
   int64_t r0 = 0, r1 = st->slot_base[kMaxSlots];
   if (a.slot_only >= 0) {
@@ -365,13 +371,21 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     if (ok) ++w_waited;
     return ok;
   };
-  auto sync_mma_w = [&](bool wait_w) -> bool {
+  auto sync_mma_w = [&](bool wait_w, bool pre_ok) -> bool {
     ++w_issued;  // this layer's weight-gradient commit
-    bool ok = tc::mbar_wait(mbar, phase);
+    bool ok = tc::mbar_wait(mbar, phase) && pre_ok;
     if (ok) phase ^= 1u;
     if (wait_w) ok = wait_w_next() && ok;
     tc::fence_after_sync();
     return !tc::bar_or(kChainBar, TT, !ok);
+  };
+  // stored activations: every MMA / epilogue thread waits for buffer gi's copy before the
+  // weight-gradient MMAs and the masks read it (false: the bounded wait gave up)
+  auto wait_act = [&](int gi) -> bool {
+    if (!SV) return true;
+    const bool ok = tc::mbar_wait(abar + gi, aphase);
+    if (ok && t == 0) a_pend &= ~(1u << gi);
+    return ok;
   };
   // after an epilogue: make smem writes visible to the tensor core and TMEM reads ordered
   auto handoff = [&]() {
@@ -550,19 +564,22 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       // the buffers' last readers (MMAs, mask loads) finished before the barrier that ended the
       // previous tile
       tc::fence_async_smem();
-      const uint32_t bytes = (Q8 ? 0u : (uint32_t)(TM * INP * 2)) + (uint32_t)ACT;
       // read once: evict first, so that the stream leaves the slot's gradient table in L2
       const uint64_t pol = tc::l2_evict_first();
-      tc::mbar_arrive_expect_tx(abar, bytes);
-      if (!Q8) tc::bulk_g2s(sm + Y::X0, ftile, TM * INP * 2, abar, pol);
-      tc::bulk_g2s(sm + Y::X1, gact + Y::A1, TM * 64 * 2, abar, pol);
-      tc::bulk_g2s(sm + Y::X2, gact + Y::A2, TM * 64 * 2, abar, pol);
+      // in the order of use, each buffer on its own barrier: a layer waits only for its input
+      auto copy = [&](int gi, uint8_t *dst, const void *src, uint32_t bytes) {
+        tc::mbar_arrive_expect_tx(abar + gi, bytes);
+        tc::bulk_g2s(dst, src, bytes, abar + gi, pol);
+        a_pend |= 1u << gi;
+      };
       if (COL) {
-        tc::bulk_g2s(sm + Y::X3, gact + Y::A3, TM * CIN * 2, abar, pol);
-        tc::bulk_g2s(sm + Y::X4, gact + Y::A4, TM * 64 * 2, abar, pol);
-        tc::bulk_g2s(sm + Y::X5, gact + Y::A5, TM * 64 * 2, abar, pol);
+        copy(0, sm + Y::X5, gact + Y::A5, TM * 64 * 2);
+        copy(1, sm + Y::X4, gact + Y::A4, TM * 64 * 2);
+        copy(2, sm + Y::X3, gact + Y::A3, TM * CIN * 2);
       }
-      a_pending = true;
+      copy(kGX2, sm + Y::X2, gact + Y::A2, TM * 64 * 2);
+      copy(kGX1, sm + Y::X1, gact + Y::A1, TM * 64 * 2);
+      if (!Q8) copy(kGX0, sm + Y::X0, ftile, TM * INP * 2);
     }
 
     // ---- features ----
@@ -684,14 +701,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     float rgb[3] = {0.f, 0.f, 0.f};
     float e0 = 0.f;  // exp(clamp(g_0, -15, 15)): the truncated-exponential gradient factor of sigma
     if constexpr (SV) {
-      // wait for the stored activations; sigma and rgb come from the forward's output
-      const bool ok = tc::mbar_wait(abar, aphase);
-      if (ok) {
-        aphase ^= 1u;
-        if (t == 0) a_pending = false;
-      }
-      abort = tc::bar_or(kChainBar, TT, !ok);
-      if (abort) break;
+      // sigma and rgb come from the forward's output (the stored activations are waited for
+      // layer by layer below)
       if (ch == 0) {
         e0 = fminf(fmaxf(fo.x, __expf(-15.f)), __expf(15.f));
         rgb[0] = fo.y;
@@ -823,11 +834,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
         mma_dx<16, 64>(tmem + Y::C_DL, s0 + Y::D3L, s0 + Y::V3);
         tc::commit(mbar);
       }
-      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued) (commit index w_issued)
+      const bool c2_ok = wait_act(0);
+      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
         mma_dw<64>(tmem + Y::C_V3, s0 + Y::D3, s0 + Y::X5, acc);
         tc::commit(wbar + (w_issued & 1u));
       }
-      abort = !sync_mma_w(false);
+      abort = !sync_mma_w(false, c2_ok);
       if (abort) break;
       epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X5, r, ch);
       handoff();
@@ -837,11 +849,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
         mma_dx<64, 64>(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::V2);
         tc::commit(mbar);
       }
-      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued) (commit index w_issued)
+      const bool c1_ok = wait_act(1);
+      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
         mma_dw<64>(tmem + Y::C_V2, s0 + Y::DA, s0 + Y::X4, acc);
         tc::commit(wbar + (w_issued & 1u));
       }
-      abort = !sync_mma_w(true);
+      abort = !sync_mma_w(true, c1_ok);
       if (abort) break;
       epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X4, r, ch);
       handoff();
@@ -851,11 +864,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
         mma_dx<64, 16>(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::V1);
         tc::commit(mbar);
       }
-      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued) (commit index w_issued)
+      const bool g_ok = wait_act(2);
+      if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
         mma_dw<CIN>(tmem + Y::C_V1, s0 + Y::DB, s0 + Y::X3, acc);
         tc::commit(wbar + (w_issued & 1u));
       }
-      abort = !sync_mma_w(true);
+      abort = !sync_mma_w(true, g_ok);
       if (abort) break;
       if (ch == 0) {
         float dg[16];
@@ -876,11 +890,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       mma_dx<16, 64>(tmem + Y::C_DL, s0 + Y::DGL, s0 + Y::W3);
       tc::commit(mbar);
     }
+    const bool h2_ok = wait_act(kGX2);
     if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
       mma_dw<64>(tmem + Y::C_W3, s0 + Y::DG, s0 + Y::X2, acc);
       tc::commit(wbar + (w_issued & 1u));
     }
-    abort = !sync_mma_w(COL);
+    abort = !sync_mma_w(COL, h2_ok);
     if (abort) break;
     epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X2, r, ch);
     handoff();
@@ -890,11 +905,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       mma_dx<64, 64>(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::W2);
       tc::commit(mbar);
     }
+    const bool h1_ok = wait_act(kGX1);
     if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
       mma_dw<64>(tmem + Y::C_W2, s0 + Y::DA, s0 + Y::X1, acc);
       tc::commit(wbar + (w_issued & 1u));
     }
-    abort = !sync_mma_w(true);
+    abort = !sync_mma_w(true, h1_ok);
     if (abort) break;
     epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X1, r, ch);
     handoff();
@@ -904,13 +920,15 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       mma_dx<64, INP>(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::W1);
       tc::commit(mbar);
     }
+    const bool f_ok = Q8 || wait_act(kGX0);  // E4M3: the first layer's codes are reloaded, not copied
     if (t == kWIssuer) {  // the weight gradient: off the chain's critical path (commit index w_issued)
       mma_dw<INP>(tmem + Y::C_W1, s0 + Y::DB, s0 + Y::X0, acc);
       tc::commit(wbar + (w_issued & 1u));
     }
-    abort = !sync_mma_w(true);
+    abort = !sync_mma_w(true, f_ok);
     if (abort) break;
     fresh = false;
+    if (SV) aphase ^= 1u;  // every buffer of this tile was waited for
     // ---- hand dfeat (D_hi + 2^-11 D_lo, binary32) to the scatter warps through DF[b] ----
     const int b = jt & 1;
     int drained = 0;
@@ -957,7 +975,9 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     while (BWD && w_waited != w_issued && wait_w_next()) {
     }
     // bounded: bulk copies still writing this CTA's shared memory land before it exits
-    if (SV && a_pending) tc::mbar_wait(abar, aphase);
+    if (SV)
+      for (int i = 0; i <= kGX0; ++i)
+        if (a_pend & (1u << i)) tc::mbar_wait(abar + i, aphase);
   } else if (BWD && cur_slot >= 0) {
     flush(cur_slot);
   }
@@ -1068,6 +1088,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
           atomicOr(&st_rw->status, kStatusTimeout);
           *abort_flag = 1;
         }
+        // the bulk store of this buffer's last tile (the older of the two pending) has read it
+        if (t == NM) tc::bulk_wait_read<1>();
         if (tc::bar_or(kGatherBar, NG, w != 0)) break;
       }
       uint8_t *fh = sm + Y::FB + b * Y::FBS, *fl = fh + TM * INP * 2;
@@ -1111,18 +1133,21 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
               pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
         }
       }
+      tc::fence_async_smem();  // the features are read by the tensor core and the bulk store
       tc::bar_sync(kGatherBar, NG);
       // the tile's features in the shared-memory layout, for the backward (high parts; low
-      // parts too unless the activations are stored)
-      uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);
-      for (int i = t - NM; i < TM * INP * 2 / 16; i += NG) {
-        __stcs(reinterpret_cast<uint4 *>(ftile) + i, reinterpret_cast<const uint4 *>(fh)[i]);
-        if (!a.acts) __stcs(reinterpret_cast<uint4 *>(ftile + TM * INP) + i, reinterpret_cast<const uint4 *>(fl)[i]);
+      // parts too unless the activations are stored): bulk stores, off the load/store unit
+      if (t == NM) {
+        uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);
+        const uint64_t pol_st = tc::l2_evict_first();  // the tables stay in L2, the features do not
+        tc::bulk_s2g(ftile, fh, TM * INP * 2, pol_st);
+        if (!a.acts) tc::bulk_s2g(ftile + TM * INP, fl, TM * INP * 2, pol_st);
+        tc::bulk_commit();
       }
-      tc::fence_async_smem();  // the features are read by the tensor core
       tc::mbar_arrive(full + b);
       ++j;
     }
+    if (t == NM) tc::bulk_wait_all();  // the shared memory stays until the stores have read it
   } else {
     // ---- MMA / epilogue warps ----
     uint32_t phase = 0;

@@ -117,6 +117,24 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
+// Bulk copy (not tensor-mapped) of `bytes` from this CTA's shared memory to global, with an L2
+// cache policy, tracked in the issuing thread's bulk async-groups (bulk_commit closes a group).
+// Same alignment rules as bulk_g2s.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes, uint64_t policy) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes), "l"(policy)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until all but the newest N bulk groups this thread committed have read their
+// shared-memory sources (those sources may then be rewritten).
+template <int N = 0>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// Wait until every bulk group this thread committed has completed (its global writes performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Bounded wait for the phase with the given parity that also gives up when *abort
 // becomes non-zero: 0 = completed, 1 = aborted, 2 = gave up after kWaitLimitNs.
 __device__ __forceinline__ int mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, const volatile int *abort) {
