@@ -13,6 +13,10 @@
 // gather a tile and then run its chain (1-3 CTAs per SM), and k_field_fws, whose
 // eight gather warps fill one of two feature buffers while its four MMA /
 // epilogue warps run the previous tile's chain (2 CTAs per SM; the default).
+// k_field_fws keeps each layer's output in tensor memory as the next layer's A
+// operand (tcgen05.mma with A from tensor memory), so its shared memory holds
+// only the feature buffers and the weights and leaves the rest of the SM's
+// 256 KB to L1, which caches the gathers' table lines.
 //
 // Backward (per tile, one CTA per SM): warps 0-7 reload the features and
 // either recompute the MLP activations or (a training step whose forward stored
@@ -158,6 +162,16 @@ __device__ __forceinline__ void mma_fwd(uint32_t d, uint32_t a, uint32_t b) {
     tc::mma_f16(d, da + (uint64_t)(j * 2 * (TM / 8) * 8), db + (uint64_t)(j * 2 * (N / 8) * 8), id, j > 0);
 }
 
+// The same with A[128 x K] in tensor memory (8 columns a K step, from a_tmem on).
+template <int K, int N>
+__device__ __forceinline__ void mma_fwd_ts(uint32_t d, uint32_t a_tmem, uint32_t b) {
+  constexpr uint32_t id = tc::idesc_f16(TM, N, 0, 0);
+  const uint64_t db = tc::desc(b, (N / 8) * 128, 128);
+#pragma unroll
+  for (int j = 0; j < K / 16; ++j)
+    tc::mma_f16_ts(d, a_tmem + (uint32_t)(j * 8), db + (uint64_t)(j * 2 * (N / 8) * 8), id, j > 0);
+}
+
 // D[128 x N] = delta[128 x K] * W, delta K-major, W stored [K rows x N] and read MN-major.
 template <int K, int N>
 __device__ __forceinline__ void mma_dx(uint32_t d, uint32_t delta, uint32_t w) {
@@ -242,6 +256,63 @@ __device__ __forceinline__ void epi64(uint32_t taddr, uint32_t taddr_lo, uint8_t
     *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
     *reinterpret_cast<uint4 *>(out_lo + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
     if (gout) __stcs(reinterpret_cast<uint4 *>(gout + off), make_uint4(o[0], o[1], o[2], o[3]));
+  }
+}
+
+// Forward epilogue into tensor memory: this thread's row and 32-column half of a [128 x 64]
+// accumulator pair, v = ReLU(D_hi + 2^-11 D_lo), written as the next layer's A operand: high
+// parts at a_hi, scaled low parts at a_lo (this thread's lane; 16 columns from column 16 ch),
+// and, if gout is given, the high parts to global in the shared-memory core layout (stored
+// activations, streaming hint).  The caller waits for the stores (tc::wait_st) before the
+// hand-off to the MMA issuer.
+__device__ __forceinline__ void epi64_tm(uint32_t taddr, uint32_t taddr_lo, uint32_t a_hi, uint32_t a_lo, int r, int ch,
+                                         uint8_t *gout) {
+  // two rounds of 16 columns: fewer values live at once than loading all 32 first
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    const int c0 = ch * 32 + hf * 16;
+    float a[16], c[16];
+    tc::ld16(taddr + c0, a);
+    tc::ld16(taddr_lo + c0, c);
+    tc::wait_ld();
+    uint32_t o[8], ol[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const float x0 = fmaxf(fmaf(c[2 * p], kLoInv, a[2 * p]), 0.f);
+      const float x1 = fmaxf(fmaf(c[2 * p + 1], kLoInv, a[2 * p + 1]), 0.f);
+      o[p] = pack_h2(x0, x1);
+      const float2 h = unpack_h2(o[p]);
+      ol[p] = pack_h2((x0 - h.x) * kLoScale, (x1 - h.y) * kLoScale);
+    }
+    tc::st8(a_hi + c0 / 2, o);
+    tc::st8(a_lo + c0 / 2, ol);
+    if (gout) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        __stcs(reinterpret_cast<uint4 *>(gout + tc::core_off(r, c0 + q * 8, TM)),
+               make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
+    }
+  }
+}
+
+// 16 floats as 8 columns of FP16 pairs in tensor memory (high parts at a_hi, scaled low parts
+// at a_lo) and, if gbuf is given, the high parts to global as the [128 x 16] core-layout row r.
+__device__ __forceinline__ void store16_tm(uint32_t a_hi, uint32_t a_lo, int r, const float (&v)[16],
+                                           uint8_t *gbuf) {
+  uint32_t o[8], ol[8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    o[p] = pack_h2(v[2 * p], v[2 * p + 1]);
+    const float2 h = unpack_h2(o[p]);
+    ol[p] = pack_h2((v[2 * p] - h.x) * kLoScale, (v[2 * p + 1] - h.y) * kLoScale);
+  }
+  tc::st8(a_hi, o);
+  tc::st8(a_lo, ol);
+  if (gbuf) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      __stcs(reinterpret_cast<uint4 *>(gbuf + tc::core_off(r, q * 8, TM)),
+             make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
   }
 }
 
@@ -994,7 +1065,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 // tile's features into the other of two feature buffers: full[b] hands buffer b to the chain,
 // and the commit of the layer-1 MMAs that read it (empty[b]) hands it back.  Two CTAs per SM
 // keep two chains in flight.  Results are those of the forward above: the same per-level
-// arithmetic, the same MMAs.
+// arithmetic, the same products (layers 2-6 read A from tensor memory instead of shared memory).
 constexpr int kWsMma = TM;                     // MMA / epilogue threads
 constexpr int kWsGather = 2 * TM;              // gather threads
 constexpr int kWsThreads = kWsMma + kWsGather;
@@ -1004,9 +1075,9 @@ template <int IN, bool VD>
 struct LW {
   static constexpr int INP = L<IN, false, VD>::INP;
   static constexpr int CIN = L<IN, false, VD>::CIN;
-  static constexpr int XL = 0;                  // [128 x 64] low parts of a layer's output
-  static constexpr int X = TM * 64 * 2;         // [128 x 64] high parts
-  static constexpr int FB = 2 * TM * 64 * 2;    // [2] features: high [128 x INP], then low
+  // layers 2-6 read their input (the previous layer's output, high and low parts) from tensor
+  // memory; only the features (layer 1's input) and the weights are in shared memory
+  static constexpr int FB = 0;                  // [2] features: high [128 x INP], then low
   static constexpr int FBS = 2 * TM * INP * 2;  // bytes of one feature buffer
   static constexpr int W1 = FB + 2 * FBS;       // weights, as in the layout above
   static constexpr int W2 = W1 + 64 * INP * 2;
@@ -1018,7 +1089,9 @@ struct LW {
   // mbarriers (MMA commit, full[2], empty[2]), TMEM address, abort flag
   static constexpr int MISC = END;
   static constexpr int SMEM = MISC + 64;
-  static constexpr uint32_t TCOLS = 128, C_DL = 64;
+  // tensor-memory columns: accumulator high parts 0..63, low parts C_DL..; a layer's output as the
+  // next layer's A operand, high parts from A_HI, low parts from A_LO (32 columns: K <= 64)
+  static constexpr uint32_t TCOLS = 256, C_DL = 64, A_HI = 128, A_LO = 160;
 };
 
 template <int IN, int G, bool COL, bool VD, int KL>
@@ -1159,7 +1232,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
       tc::fence_after_sync();
       return !tc::bar_or(kChainBar, NM, !ok);
     };
+    // after an epilogue: its tensor-memory stores complete, shared-memory writes visible to the
+    // tensor core, then the barrier
     auto handoff = [&]() {
+      tc::wait_st();
       tc::fence_async_smem();
       tc::fence_before_sync();
       tc::bar_sync(kChainBar, NM);
@@ -1209,21 +1285,21 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
       abort = !sync_mma();
       if (abort) break;
       for (int c = 0; c < 2; ++c)
-        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A1 : nullptr);
+        epi64_tm(trow, trow + Y::C_DL, trow + Y::A_HI, trow + Y::A_LO, r, c, gact ? gact + A::A1 : nullptr);
       handoff();
       if (t == 0) {
-        mma_fwd<64, 64>(tmem, s0 + Y::X, s0 + Y::W2);
-        mma_fwd<64, 64>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W2);
+        mma_fwd_ts<64, 64>(tmem, tmem + Y::A_HI, s0 + Y::W2);
+        mma_fwd_ts<64, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::W2);
         tc::commit(mbar);
       }
       abort = !sync_mma();
       if (abort) break;
       for (int c = 0; c < 2; ++c)
-        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A2 : nullptr);
+        epi64_tm(trow, trow + Y::C_DL, trow + Y::A_HI, trow + Y::A_LO, r, c, gact ? gact + A::A2 : nullptr);
       handoff();
       if (t == 0) {
-        mma_fwd<64, 16>(tmem, s0 + Y::X, s0 + Y::W3);
-        mma_fwd<64, 16>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::W3);
+        mma_fwd_ts<64, 16>(tmem, tmem + Y::A_HI, s0 + Y::W3);
+        mma_fwd_ts<64, 16>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::W3);
         tc::commit(mbar);
       }
       abort = !sync_mma();
@@ -1231,7 +1307,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
       float g[16];
       float rgb[3] = {0.f, 0.f, 0.f};
       ld16_pair(trow, trow + Y::C_DL, g);
-      store16(sm + Y::X, sm + Y::XL, r, g, (COL && gact) ? gact + A::A3 : nullptr);
+      store16_tm(trow + Y::A_HI, trow + Y::A_LO, r, g, (COL && gact) ? gact + A::A3 : nullptr);
       if (!COL) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) rgb[k] = sigm(g[1 + k]);
@@ -1245,33 +1321,33 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
           for (int q = 0; q < 3; ++q) dir[q] = a.ray_od[(int64_t)(3 + q) * a.n_rays + ray];
         }
         sh16(dir[0], dir[1], dir[2], y);
-        store16(sm + Y::X + TM * 16 * 2, sm + Y::XL + TM * 16 * 2, r, y, gact ? gact + A::A3 + TM * 16 * 2 : nullptr);
+        store16_tm(trow + Y::A_HI + 8, trow + Y::A_LO + 8, r, y, gact ? gact + A::A3 + TM * 16 * 2 : nullptr);
       }
       handoff();
       if (COL) {
         if (t == 0) {
-          mma_fwd<CIN, 64>(tmem, s0 + Y::X, s0 + Y::V1);
-          mma_fwd<CIN, 64>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V1);
+          mma_fwd_ts<CIN, 64>(tmem, tmem + Y::A_HI, s0 + Y::V1);
+          mma_fwd_ts<CIN, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::V1);
           tc::commit(mbar);
         }
         abort = !sync_mma();
         if (abort) break;
         for (int c = 0; c < 2; ++c)
-        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A4 : nullptr);
+        epi64_tm(trow, trow + Y::C_DL, trow + Y::A_HI, trow + Y::A_LO, r, c, gact ? gact + A::A4 : nullptr);
         handoff();
         if (t == 0) {
-          mma_fwd<64, 64>(tmem, s0 + Y::X, s0 + Y::V2);
-          mma_fwd<64, 64>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V2);
+          mma_fwd_ts<64, 64>(tmem, tmem + Y::A_HI, s0 + Y::V2);
+          mma_fwd_ts<64, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::V2);
           tc::commit(mbar);
         }
         abort = !sync_mma();
         if (abort) break;
         for (int c = 0; c < 2; ++c)
-        epi64<0>(trow, trow + Y::C_DL, sm + Y::X, sm + Y::XL, nullptr, r, c, 1.0f, gact ? gact + A::A5 : nullptr);
+        epi64_tm(trow, trow + Y::C_DL, trow + Y::A_HI, trow + Y::A_LO, r, c, gact ? gact + A::A5 : nullptr);
         handoff();
         if (t == 0) {
-          mma_fwd<64, 16>(tmem, s0 + Y::X, s0 + Y::V3);
-          mma_fwd<64, 16>(tmem + Y::C_DL, s0 + Y::XL, s0 + Y::V3);
+          mma_fwd_ts<64, 16>(tmem, tmem + Y::A_HI, s0 + Y::V3);
+          mma_fwd_ts<64, 16>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::V3);
           tc::commit(mbar);
         }
         abort = !sync_mma();
