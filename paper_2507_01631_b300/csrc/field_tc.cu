@@ -13,10 +13,10 @@
 // gather a tile and then run its chain (1-3 CTAs per SM), and k_field_fws, whose
 // eight gather warps fill one of two feature buffers while its four MMA /
 // epilogue warps run the previous tile's chain (2 CTAs per SM; the default).
-// k_field_fws keeps each layer's output in tensor memory as the next layer's A
-// operand (tcgen05.mma with A from tensor memory), so its shared memory holds
-// only the feature buffers and the weights and leaves the rest of the SM's
-// 256 KB to L1, which caches the gathers' table lines.
+// k_field_fws keeps its features and each layer's output in tensor memory as
+// the next layer's A operand (tcgen05.mma with A from tensor memory), so its
+// shared memory holds only the weights and leaves the rest of the SM's 256 KB
+// to L1, which caches the gathers' table lines.
 //
 // Backward (per tile, one CTA per SM): warps 0-7 reload the features and
 // either recompute the MLP activations or (a training step whose forward stored
@@ -1062,7 +1062,8 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 // ---- forward with dedicated gather warps ---------------------------------------
 // Four MMA / epilogue warps (one thread a tile row, both column halves) run one tile's MLP
 // chain while eight gather warps (one thread a sample and level parity) interpolate the next
-// tile's features into the other of two feature buffers: full[b] hands buffer b to the chain,
+// tile's features into the other of two tensor-memory feature buffers (a gather warp writes the
+// lanes of its 32 samples, as tcgen05.st requires): full[b] hands buffer b to the chain,
 // and the commit of the layer-1 MMAs that read it (empty[b]) hands it back.  Two CTAs per SM
 // keep two chains in flight.  Results are those of the forward above: the same per-level
 // arithmetic, the same products (layers 2-6 read A from tensor memory instead of shared memory).
@@ -1075,11 +1076,9 @@ template <int IN, bool VD>
 struct LW {
   static constexpr int INP = L<IN, false, VD>::INP;
   static constexpr int CIN = L<IN, false, VD>::CIN;
-  // layers 2-6 read their input (the previous layer's output, high and low parts) from tensor
-  // memory; only the features (layer 1's input) and the weights are in shared memory
-  static constexpr int FB = 0;                  // [2] features: high [128 x INP], then low
-  static constexpr int FBS = 2 * TM * INP * 2;  // bytes of one feature buffer
-  static constexpr int W1 = FB + 2 * FBS;       // weights, as in the layout above
+  // every layer reads its input (high and low parts) from tensor memory: shared memory holds
+  // only the weights (B operands), the rest of the SM's 256 KB is L1 for the table gathers
+  static constexpr int W1 = 0;                  // weights, as in the layout above
   static constexpr int W2 = W1 + 64 * INP * 2;
   static constexpr int W3 = W2 + 64 * 64 * 2;
   static constexpr int V1 = W3 + 16 * 64 * 2;
@@ -1090,8 +1089,11 @@ struct LW {
   static constexpr int MISC = END;
   static constexpr int SMEM = MISC + 64;
   // tensor-memory columns: accumulator high parts 0..63, low parts C_DL..; a layer's output as the
-  // next layer's A operand, high parts from A_HI, low parts from A_LO (32 columns: K <= 64)
-  static constexpr uint32_t TCOLS = 256, C_DL = 64, A_HI = 128, A_LO = 160;
+  // next layer's A operand, high parts from A_HI, low parts from A_LO (32 columns: K <= 64); the
+  // two feature buffers (layer 1's A operand) from F0, buffer b's high parts at F0 + 32 b, low
+  // parts 16 columns further (K = INP <= 32); level l's two features are column l
+  static constexpr uint32_t TCOLS = 256, C_DL = 64, A_HI = 128, A_LO = 160, F0 = 192;
+  static_assert(INP <= 32, "feature buffers of 16 columns");
 };
 
 template <int IN, int G, bool COL, bool VD, int KL>
@@ -1126,7 +1128,6 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, Y::TCOLS);
-  // zero every buffer once: the feature buffers' padding columns (IN .. INP-1) stay zero
   for (int i = t; i < Y::END / 16; i += blockDim.x) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_before_sync();
   __syncthreads();
@@ -1147,6 +1148,15 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
     const int s = (t - NM) % TM, lq = (t - NM) / TM;  // sample of the tile, level parity
     constexpr int LS = NG / TM;                        // level groups (2)
     const uint64_t keep = l2_keep();                   // the tables stay in L2
+    // this thread's lane of the feature buffers: the padding columns of layer 1's K (features
+    // IN .. INP-1) are zero once and for all
+    if (lq == 0 && IN < INP) {
+      for (int b = 0; b < 2; ++b)
+        for (int c = IN / 2; c < INP / 2; ++c) {
+          tc::st1(trow + Y::F0 + 32 * b + c, 0u);
+          tc::st1(trow + Y::F0 + 32 * b + 16 + c, 0u);
+        }
+    }
     int j = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const int64_t ts = r0 + tile * TM;
@@ -1161,11 +1171,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
           atomicOr(&st_rw->status, kStatusTimeout);
           *abort_flag = 1;
         }
-        // the bulk store of this buffer's last tile (the older of the two pending) has read it
-        if (t == NM) tc::bulk_wait_read<1>();
         if (tc::bar_or(kGatherBar, NG, w != 0)) break;
+        tc::fence_after_sync();  // the tensor-memory writes below follow the MMAs' reads
       }
-      uint8_t *fh = sm + Y::FB + b * Y::FBS, *fl = fh + TM * INP * 2;
+      const uint32_t fh = trow + Y::F0 + 32 * b, fl = fh + 16;  // this warp's lanes of buffer b
       const int64_t slot_end = (int64_t)st->slot_base[slot] + st->slot_count[slot];
       const int64_t sidx = ts + s;
       const bool sval = sidx < slot_end && sidx < r1;
@@ -1201,26 +1210,33 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
           const float f0 = f.x, f1 = f.y;
           const uint32_t hp = pack_h2(f0, f1);
           const float2 hh = unpack_h2(hp);
-          *reinterpret_cast<uint32_t *>(fh + tc::core_off(s, 2 * l, TM)) = hp;
-          *reinterpret_cast<uint32_t *>(fl + tc::core_off(s, 2 * l, TM)) =
-              pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale);
+          tc::st1(fh + l, hp);
+          tc::st1(fl + l, pack_h2((f0 - hh.x) * kLoScale, (f1 - hh.y) * kLoScale));
         }
       }
-      tc::fence_async_smem();  // the features are read by the tensor core and the bulk store
+      tc::wait_st();
+      tc::fence_before_sync();
       tc::bar_sync(kGatherBar, NG);
-      // the tile's features in the shared-memory layout, for the backward (high parts; low
-      // parts too unless the activations are stored): bulk stores, off the load/store unit
-      if (t == NM) {
-        uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP);
-        const uint64_t pol_st = tc::l2_evict_first();  // the tables stay in L2, the features do not
-        tc::bulk_s2g(ftile, fh, TM * INP * 2, pol_st);
-        if (!a.acts) tc::bulk_s2g(ftile + TM * INP, fl, TM * INP * 2, pol_st);
-        tc::bulk_commit();
+      tc::fence_after_sync();
+      // the tile's features, for the backward, in the shared-memory core layout the backward
+      // copies them into: high parts (the level-parity-0 threads), and low parts (parity 1)
+      // unless the activations are stored; each thread writes its sample's row
+      if (lq == 0 || !a.acts) {
+        uint16_t *ftile = a.feat_lp + (ts / TM) * (int64_t)(2 * TM * INP) + (lq ? TM * INP : 0);
+        uint8_t *frow = reinterpret_cast<uint8_t *>(ftile);
+#pragma unroll
+        for (int c = 0; c < INP / 2; c += 8) {
+          uint32_t v[8];
+          tc::ld8((lq ? fl : fh) + c, v);
+          tc::wait_ld();
+          __stcs(reinterpret_cast<uint4 *>(frow + tc::core_off(s, 2 * c, TM)), make_uint4(v[0], v[1], v[2], v[3]));
+          __stcs(reinterpret_cast<uint4 *>(frow + tc::core_off(s, 2 * c + 8, TM)), make_uint4(v[4], v[5], v[6], v[7]));
+        }
       }
+      tc::fence_before_sync();
       tc::mbar_arrive(full + b);
       ++j;
     }
-    if (t == NM) tc::bulk_wait_all();  // the shared memory stays until the stores have read it
   } else {
     // ---- MMA / epilogue warps ----
     uint32_t phase = 0;
@@ -1274,10 +1290,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_field_fws(const FieldArgs a) 
         tc::fence_after_sync();
         if (abort) break;
       }
-      const uint32_t fh = s0 + Y::FB + b * Y::FBS, fl = fh + TM * INP * 2;
+      const uint32_t fh = tmem + Y::F0 + 32 * b, fl = fh + 16;
       if (t == 0) {
-        mma_fwd<INP, 64>(tmem, fh, s0 + Y::W1);
-        mma_fwd<INP, 64>(tmem + Y::C_DL, fl, s0 + Y::W1);
+        mma_fwd_ts<INP, 64>(tmem, fh, s0 + Y::W1);
+        mma_fwd_ts<INP, 64>(tmem + Y::C_DL, fl, s0 + Y::W1);
         tc::commit(mbar);
         tc::commit(empty + b);
       }
@@ -1377,7 +1393,7 @@ cudaError_t launch_ws(const FieldArgs &a, int sm_count, cudaStream_t st) {
   using Y = LW<IN, VD>;
   static_assert(2 * (Y::SMEM + 1024) <= 233472, "two CTAs per SM: shared memory");
   static_assert(2 * Y::TCOLS <= 512, "two CTAs per SM: tensor memory");
-  static_assert(Y::FB % 1024 == 0 && Y::FBS % 16 == 0 && Y::W1 % 16 == 0 && Y::MISC % 8 == 0, "alignment");
+  static_assert(Y::W1 % 16 == 0 && Y::MISC % 8 == 0, "alignment");
   auto k = k_field_fws<IN, G, COL, VD, KL>;
   static std::atomic<uint32_t> attr_done{0};  // per instantiation: devices whose limit is set
   if (cudaError_t e = set_smem_limit(k, Y::SMEM, attr_done); e != cudaSuccess) return e;
