@@ -15,8 +15,8 @@
 // epilogue warps run the previous tile's chain (2 CTAs per SM; the default).
 // k_field_fws keeps its features and each layer's output in tensor memory as
 // the next layer's A operand (tcgen05.mma with A from tensor memory), so its
-// shared memory holds only the weights and leaves the rest of the SM's 256 KB
-// to L1, which caches the gathers' table lines.
+// shared memory holds only the weights and its operands stay out of the L1TEX
+// data pipe that its table gathers need.
 //
 // Backward (per tile, one CTA per SM): warps 0-7 reload the features and
 // either recompute the MLP activations or (a training step whose forward stored
@@ -1077,7 +1077,8 @@ struct LW {
   static constexpr int INP = L<IN, false, VD>::INP;
   static constexpr int CIN = L<IN, false, VD>::CIN;
   // every layer reads its input (high and low parts) from tensor memory: shared memory holds
-  // only the weights (B operands), the rest of the SM's 256 KB is L1 for the table gathers
+  // only the weights (B operands), and no operand traffic competes with the table gathers
+  // in the L1TEX data pipe
   static constexpr int W1 = 0;                  // weights, as in the layout above
   static constexpr int W2 = W1 + 64 * INP * 2;
   static constexpr int W3 = W2 + 64 * 64 * 2;
