@@ -91,7 +91,9 @@ struct L {
   static constexpr int DB = BWD ? DA + TM * 64 * 2 : 0;        // [128 x 64]
   static constexpr int DG = BWD ? DB + TM * 64 * 2 : 0;        // [128 x 16]
   static constexpr int D3 = BWD ? DG + TM * 16 * 2 : 0;        // [128 x 16]
-  // Low parts (x 2^11): of the forward operands while the forward runs, then of the deltas.
+  // Low parts (x 2^11) of the forward operands, while the forward runs (in a forward or a
+  // recomputing backward; the deltas' low parts are in tensor memory, A_LO; the region also keeps
+  // the dW MMAs' padded reads past the delta buffers inside the allocation).
   // The forward keeps one [128 x 64] buffer for every operand (hi and lo): a layer's epilogue
   // runs only after the MMA that read the layer's input has completed, so the output can
   // overwrite it.  The backward keeps every activation for its weight-gradient MMAs.
@@ -100,7 +102,6 @@ struct L {
   static constexpr int XLA = BWD ? XL0 + TM * INP * 2 : LO;    // [128 x 64] h1, then c1
   static constexpr int XLB = BWD ? XLA + TM * 64 * 2 : LO;     // [128 x 64] h2, then g, then c2
   static constexpr int XL3 = XLB;
-  static constexpr int DAL = LO, DBL = LO + TM * 64 * 2, DGL = LO + 2 * TM * 64 * 2, D3L = DGL + TM * 16 * 2;
   static constexpr int LO_END =
       LO + (BWD ? cmax(TM * INP * 2 + 2 * TM * 64 * 2, 2 * TM * 64 * 2 + 2 * TM * 16 * 2) : TM * 64 * 2);
   // high parts of the forward operands
@@ -130,6 +131,10 @@ struct L {
   // tensor-memory columns: 0..63 accumulator of the high parts; C_DL the low parts
   static constexpr uint32_t C_W1 = 64, C_W2 = 128, C_W3 = 192, C_V2 = 256, C_V3 = 320, C_V1 = 384;
   static constexpr uint32_t C_DL = BWD ? 448 : 64;
+  // backward: the scaled low parts of a layer's delta, the A operand of the next input-gradient
+  // MMA (K <= 64: 32 columns, between dW1's accumulator and dW2's)
+  static constexpr uint32_t A_LO = 96;
+  static_assert(!BWD || (C_W1 + INP <= A_LO && A_LO + 32 <= C_W2), "tensor-memory columns of the delta low parts");
   // Stored activations of a tile (high parts, FP16, in the layout above), written by the
   // forward of a training step and copied back by the backward instead of recomputed:
   // h1, h2 [128 x 64], then with a colour network g [128 x CIN], c1, c2 [128 x 64].
@@ -190,6 +195,15 @@ __device__ __forceinline__ void mma_dw(uint32_t d, uint32_t delta, uint32_t x, u
 #pragma unroll
   for (int j = 0; j < TM / 16; ++j)
     tc::mma_f16(d, da + (uint64_t)(j * 16), db + (uint64_t)(j * 16), id, (j > 0) || accumulate);
+}
+
+// The same with delta in tensor memory (8 columns a K step from a_tmem).
+template <int K, int N>
+__device__ __forceinline__ void mma_dx_ts(uint32_t d, uint32_t a_tmem, uint32_t w) {
+  constexpr uint32_t id = tc::idesc_f16(TM, N, 0, 1);
+  const uint64_t db = tc::desc(w, 128, (K / 8) * 128);
+#pragma unroll
+  for (int j = 0; j < K / 16; ++j) tc::mma_f16_ts(d, a_tmem + (uint32_t)(j * 8), db + (uint64_t)(j * 16), id, j > 0);
 }
 
 // Copy a row-major [rows x cols] 16-bit matrix from global into the core layout (R = rpad rows,
@@ -314,6 +328,63 @@ __device__ __forceinline__ void store16_tm(uint32_t a_hi, uint32_t a_lo, int r, 
       __stcs(reinterpret_cast<uint4 *>(gbuf + tc::core_off(r, q * 8, TM)),
              make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
   }
+}
+
+// Backward epilogue: as epi64<1> (this thread's row and column half of a [128 x 64]
+// accumulator pair, v = D_hi + 2^-11 D_lo kept where the [128 x 64] activation mask is positive),
+// the high parts to shared memory (out: the weight-gradient MMA and the next input-gradient MMA
+// read them) and the scaled low parts to tensor memory (a_lo, this thread's lane, 16 columns from
+// column 16 ch: only the next input-gradient MMA reads them).  The caller waits for the tensor-
+// memory stores (tc::wait_st) before the hand-off.
+__device__ __forceinline__ void epi64_bwd(uint32_t taddr, uint32_t taddr_lo, uint8_t *out, uint32_t a_lo,
+                                          const uint8_t *mask, int r, int ch) {
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    const int c0 = ch * 32 + hf * 16;
+    float a[16], c[16];
+    tc::ld16(taddr + c0, a);
+    tc::ld16(taddr_lo + c0, c);
+    tc::wait_ld();
+    uint32_t ol[8];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t off = tc::core_off(r, c0 + q * 8, TM);
+      const uint4 m4 = *reinterpret_cast<const uint4 *>(mask + off);
+      const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+      uint32_t o[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float2 mk = unpack_h2(mw[p]);
+        const int i = q * 8 + 2 * p;
+        const float x0 = mk.x > 0.f ? fmaf(c[i], kLoInv, a[i]) : 0.f;
+        const float x1 = mk.y > 0.f ? fmaf(c[i + 1], kLoInv, a[i + 1]) : 0.f;
+        o[p] = pack_h2(x0, x1);
+        const float2 h = unpack_h2(o[p]);
+        ol[q * 4 + p] = pack_h2((x0 - h.x) * kLoScale, (x1 - h.y) * kLoScale);
+      }
+      *reinterpret_cast<uint4 *>(out + off) = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+    tc::st8(a_lo + c0 / 2, ol);
+  }
+}
+
+// 16 floats as one FP16 row segment of a [128 x 16] shared buffer (high parts) and their scaled
+// low parts as 8 tensor-memory columns of this thread's lane at a_lo.
+__device__ __forceinline__ void store16_bwd(uint8_t *buf, uint32_t a_lo, int r, const float (&v)[16]) {
+  uint32_t ol[8];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    uint32_t o[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int i = q * 8 + 2 * p;
+      o[p] = pack_h2(v[i], v[i + 1]);
+      const float2 h = unpack_h2(o[p]);
+      ol[q * 4 + p] = pack_h2((v[i] - h.x) * kLoScale, (v[i + 1] - h.y) * kLoScale);
+    }
+    *reinterpret_cast<uint4 *>(buf + tc::core_off(r, q * 8, TM)) = make_uint4(o[0], o[1], o[2], o[3]);
+  }
+  tc::st8(a_lo, ol);
 }
 
 // 16 columns of an accumulator pair, combined: v = D_hi + 2^-11 D_lo.
@@ -460,6 +531,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
   };
   // after an epilogue: make smem writes visible to the tensor core and TMEM reads ordered
   auto handoff = [&]() {
+    tc::wait_st();  // the backward's delta low parts in tensor memory
     tc::fence_async_smem();
     tc::fence_before_sync();
     tc::bar_sync(kChainBar, TT);
@@ -887,13 +959,13 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       if (COL) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) row[k] = d3[k];
-        store16(sm + Y::D3, sm + Y::D3L, r, row);
+        store16_bwd(sm + Y::D3, trow + Y::A_LO, r, row);
         g[0] = dg0;  // keep dsigma's contribution to dg_0 for later
       } else {
         row[0] = dg0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) row[1 + k] = d3[k];
-        store16(sm + Y::DG, sm + Y::DGL, r, row);
+        store16_bwd(sm + Y::DG, trow + Y::A_LO, r, row);
       }
     }
     handoff();
@@ -902,7 +974,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       // dc2 = delta3 * V3, dV3 += delta3^T c2
       if (t == 0) {
         mma_dx<16, 64>(tmem, s0 + Y::D3, s0 + Y::V3);
-        mma_dx<16, 64>(tmem + Y::C_DL, s0 + Y::D3L, s0 + Y::V3);
+        mma_dx_ts<16, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::V3);
         tc::commit(mbar);
       }
       const bool c2_ok = wait_act(0);
@@ -912,12 +984,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       }
       abort = !sync_mma_w(false, c2_ok);
       if (abort) break;
-      epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X5, r, ch);
+      epi64_bwd(trow, trow + Y::C_DL, sm + Y::DA, trow + Y::A_LO, sm + Y::X5, r, ch);
       handoff();
       // dc1 = delta_c2 * V2, dV2 += delta_c2^T c1
       if (t == 0) {
         mma_dx<64, 64>(tmem, s0 + Y::DA, s0 + Y::V2);
-        mma_dx<64, 64>(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::V2);
+        mma_dx_ts<64, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::V2);
         tc::commit(mbar);
       }
       const bool c1_ok = wait_act(1);
@@ -927,12 +999,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
       }
       abort = !sync_mma_w(true, c1_ok);
       if (abort) break;
-      epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X4, r, ch);
+      epi64_bwd(trow, trow + Y::C_DL, sm + Y::DB, trow + Y::A_LO, sm + Y::X4, r, ch);
       handoff();
       // dg = delta_c1 * V1 (+ dsigma term; N = 16: the g columns of V1), dV1 += delta_c1^T [g | SH]
       if (t == 0) {
         mma_dx<64, 16>(tmem, s0 + Y::DB, s0 + Y::V1);
-        mma_dx<64, 16>(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::V1);
+        mma_dx_ts<64, 16>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::V1);
         tc::commit(mbar);
       }
       const bool g_ok = wait_act(2);
@@ -951,14 +1023,14 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 #pragma unroll
         for (int i = 0; i < 16; ++i) dg[i] = fmaf(dgl[i], kLoInv, dg[i]);
         dg[0] += g[0];
-        store16(sm + Y::DG, sm + Y::DGL, r, dg);
+        store16_bwd(sm + Y::DG, trow + Y::A_LO, r, dg);
       }
       handoff();
     }
     // dh2 = delta_g * W3 (masked by h2), dW3 += delta_g^T h2 (the first layer without a colour net)
     if (t == 0) {
       mma_dx<16, 64>(tmem, s0 + Y::DG, s0 + Y::W3);
-      mma_dx<16, 64>(tmem + Y::C_DL, s0 + Y::DGL, s0 + Y::W3);
+      mma_dx_ts<16, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::W3);
       tc::commit(mbar);
     }
     const bool h2_ok = wait_act(kGX2);
@@ -968,12 +1040,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     }
     abort = !sync_mma_w(COL, h2_ok);
     if (abort) break;
-    epi64<1>(trow, trow + Y::C_DL, sm + Y::DA, sm + Y::DAL, sm + Y::X2, r, ch);
+    epi64_bwd(trow, trow + Y::C_DL, sm + Y::DA, trow + Y::A_LO, sm + Y::X2, r, ch);
     handoff();
     // dh1 = delta_h2 * W2 (masked by h1), dW2 += delta_h2^T h1
     if (t == 0) {
       mma_dx<64, 64>(tmem, s0 + Y::DA, s0 + Y::W2);
-      mma_dx<64, 64>(tmem + Y::C_DL, s0 + Y::DAL, s0 + Y::W2);
+      mma_dx_ts<64, 64>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::W2);
       tc::commit(mbar);
     }
     const bool h1_ok = wait_act(kGX1);
@@ -983,12 +1055,12 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
     }
     abort = !sync_mma_w(true, h1_ok);
     if (abort) break;
-    epi64<1>(trow, trow + Y::C_DL, sm + Y::DB, sm + Y::DBL, sm + Y::X1, r, ch);
+    epi64_bwd(trow, trow + Y::C_DL, sm + Y::DB, trow + Y::A_LO, sm + Y::X1, r, ch);
     handoff();
     // dfeat = delta_h1 * W1, dW1 += delta_h1^T feat
     if (t == 0) {
       mma_dx<64, INP>(tmem, s0 + Y::DB, s0 + Y::W1);
-      mma_dx<64, INP>(tmem + Y::C_DL, s0 + Y::DBL, s0 + Y::W1);
+      mma_dx_ts<64, INP>(tmem + Y::C_DL, tmem + Y::A_LO, s0 + Y::W1);
       tc::commit(mbar);
     }
     const bool f_ok = Q8 || wait_act(kGX0);  // E4M3: the first layer's codes are reloaded, not copied
