@@ -186,8 +186,8 @@ def field_forward_work(w, precision, saved=False):
 # traffic null.
 WINDOW_CAPTURE = "window2x2_full, 65536 rays (7.98 M samples)"
 TILE_CAPTURE = "tile512_full, 32768 rays (2.86 M samples)"
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_forward", True, "split"): (704.0, WINDOW_CAPTURE),
-                            ("mixed", "field_backward", True, ""): (789.9, WINDOW_CAPTURE),
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_forward", True, "split"): (704.2, WINDOW_CAPTURE),
+                            ("mixed", "field_backward", True, ""): (787.9, WINDOW_CAPTURE),
                             ("fp32", "field_backward", False, ""): (736.6, TILE_CAPTURE),
                             ("fp32", "field_forward", False, ""): (42.5, TILE_CAPTURE)}
 
@@ -426,7 +426,7 @@ def reduction_probe(torch, snk, ctx, n_entries, reps=3):
 # lts__t_sectors_op_red also counts the half of them that cross to the other die's L2 a second time)
 # over the samples of the launch, keyed by (precision, stored activations), with the capture.  The
 # probe's rate is in the same unit.  A kernel changed since its capture has no entry.
-MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (69.5, WINDOW_CAPTURE)}
+MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (69.4, WINDOW_CAPTURE)}
 
 
 def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=None):
