@@ -1138,7 +1138,7 @@ __global__ void __launch_bounds__(BWD ? TT + scatter_threads(SV) : TT, MINB) k_f
 // lanes of its 32 samples, as tcgen05.st requires): full[b] hands buffer b to the chain,
 // and the commit of the layer-1 MMAs that read it (empty[b]) hands it back.  Two CTAs per SM
 // keep two chains in flight.  Results are those of the forward above: the same per-level
-// arithmetic, the same products (layers 2-6 read A from tensor memory instead of shared memory).
+// arithmetic, the same products (every layer reads A from tensor memory instead of shared memory).
 constexpr int kWsMma = TM;                     // MMA / epilogue threads
 constexpr int kWsGather = 2 * TM;              // gather threads
 constexpr int kWsThreads = kWsMma + kWsGather;
