@@ -428,6 +428,14 @@ def reduction_probe(torch, snk, ctx, n_entries, reps=3):
 # probe's rate is in the same unit.  A kernel changed since its capture has no entry.
 MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (69.4, WINDOW_CAPTURE)}
 
+# Table-gather sectors per sample of the forward with dedicated gather warps: ncu
+# l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum (requested from L1) and
+# lts__t_sectors_srcunit_tex_op_read.sum (reaching L2: L1 misses and the streams) over the samples,
+# keyed by (precision, stored activations, split forward), with the capture.  The method's own
+# gather is 8 corners x L x F FP16 = 512 B a sample, 16 sectors if every corner pair shared one.
+GATHER_CAPTURE = "window2x2_full, 16384 rays (1.99 M samples), --set full"
+MEASURED_GATHER_SECTORS_PER_SAMPLE = {("mixed", True, 1): (65.3, 45.8, GATHER_CAPTURE)}
+
 
 def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=None):
     """The dominant kernel's roofline: achieved = the method's algorithmic bytes per sample x
@@ -639,6 +647,17 @@ def run_ours(args, w):
                         "achieved": step_bytes * per_step_samples / step_s / 1e9, "unit": "GB/s",
                         "frac": step_bytes * per_step_samples / step_s / 1e9 / pk["hbm_gbs"]}
         roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
+        if name != "field_forward" and "field_forward" in stages:
+            # the second field kernel beside the dominant one, with its gather sectors
+            fs, fc = stages["field_forward"]
+            split = tuning.get("tc_fwd_split", 0)
+            fwd = roofline_of(w, prec_key, "field_forward", (fs / max(fc, 1)) / 1000.0, per_step_samples, saved,
+                              split, pk, None)
+            g = MEASURED_GATHER_SECTORS_PER_SAMPLE.get((prec_key, bool(saved), int(split)))
+            if g is not None:
+                fwd["gather_sectors_per_sample"] = {"l1_requested": g[0], "l2_read": g[1], "method": 16,
+                                                    "source": "ncu, %s" % g[2]}
+            roof["field_forward"] = fwd
 
     cpu = None
     if not args.no_cpu_baseline:

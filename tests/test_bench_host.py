@@ -17,6 +17,13 @@ def test_dram_figures_cover_the_default_configurations_only():
     assert bench.dram_bytes_per_sample("mixed_e4m3", "field_backward", True, 0) is None
 
 
+def test_gather_sectors_cover_the_default_forward_only():
+    # the default forward (stored activations, dedicated gather warps) has its capture; others none
+    assert bench.MEASURED_GATHER_SECTORS_PER_SAMPLE.get(("mixed", True, 1)) is not None
+    assert bench.MEASURED_GATHER_SECTORS_PER_SAMPLE.get(("mixed", True, 0)) is None
+    assert bench.MEASURED_GATHER_SECTORS_PER_SAMPLE.get(("fp32", False, 0)) is None
+
+
 def test_method_bytes_of_the_headline_workload_by_hand():
     """The survey's algorithmic bytes per sample for L = 16 levels x F = 2 features: the gather
     reads 8 corners x 16 x 2 FP16 = 512 B (binary32 tables: 1024 B), the scatter adds 8 x 16 x 2
