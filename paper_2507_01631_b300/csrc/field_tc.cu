@@ -142,6 +142,25 @@ struct L {
   __host__ __device__ static constexpr int act_bytes(bool col) { return col ? A5 + TM * 64 * 2 : A3; }
 };
 
+// Paired binary32 arithmetic (fma / mul .rn.f32x2): two lanes of IEEE binary32, each rounded as
+// the scalar instruction would round it.
+__device__ __forceinline__ uint64_t f2pk(float a, float b) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ void f2upk(uint64_t v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t fmul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   const __half2 v = __floats2half2_rn(a, b);
   return *reinterpret_cast<const uint32_t *>(&v);
@@ -290,13 +309,20 @@ __device__ __forceinline__ void epi64_tm(uint32_t taddr, uint32_t taddr_lo, uint
     tc::ld16(taddr_lo + c0, c);
     tc::wait_ld();
     uint32_t o[8], ol[8];
+    const uint64_t inv2 = f2pk(kLoInv, kLoInv), sc2 = f2pk(kLoScale, kLoScale), nsc2 = f2pk(-kLoScale, -kLoScale);
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
-      const float x0 = fmaxf(fmaf(c[2 * p], kLoInv, a[2 * p]), 0.f);
-      const float x1 = fmaxf(fmaf(c[2 * p + 1], kLoInv, a[2 * p + 1]), 0.f);
+      // v = D_hi + 2^-11 D_lo, ReLU, high part h = FP16(v), scaled low part (v - h) 2^11 computed as
+      // fma(-h, 2^11, v 2^11): exact, as the difference and the power-of-two scaling are
+      float x0, x1;
+      f2upk(ffma2(f2pk(c[2 * p], c[2 * p + 1]), inv2, f2pk(a[2 * p], a[2 * p + 1])), x0, x1);
+      x0 = fmaxf(x0, 0.f);
+      x1 = fmaxf(x1, 0.f);
       o[p] = pack_h2(x0, x1);
       const float2 h = unpack_h2(o[p]);
-      ol[p] = pack_h2((x0 - h.x) * kLoScale, (x1 - h.y) * kLoScale);
+      float l0, l1;
+      f2upk(ffma2(f2pk(h.x, h.y), nsc2, fmul2(f2pk(x0, x1), sc2)), l0, l1);
+      ol[p] = pack_h2(l0, l1);
     }
     tc::st8(a_hi + c0 / 2, o);
     tc::st8(a_lo + c0 / 2, ol);
