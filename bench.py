@@ -186,8 +186,8 @@ def field_forward_work(w, precision, saved=False):
 # traffic null.
 WINDOW_CAPTURE = "window2x2_full, 65536 rays (7.98 M samples)"
 TILE_CAPTURE = "tile512_full, 32768 rays (2.86 M samples)"
-MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_forward", True, "split"): (704.2, WINDOW_CAPTURE),
-                            ("mixed", "field_backward", True, ""): (787.9, WINDOW_CAPTURE),
+MEASURED_DRAM_PER_SAMPLE = {("mixed", "field_forward", True, "split"): (702.4, WINDOW_CAPTURE),
+                            ("mixed", "field_backward", True, ""): (787.7, WINDOW_CAPTURE),
                             ("fp32", "field_backward", False, ""): (736.6, TILE_CAPTURE),
                             ("fp32", "field_forward", False, ""): (42.5, TILE_CAPTURE)}
 
@@ -434,7 +434,7 @@ MEASURED_RED_SECTORS_PER_SAMPLE = {("mixed", True): (69.4, WINDOW_CAPTURE)}
 # keyed by (precision, stored activations, split forward), with the capture.  The method's own
 # gather is 8 corners x L x F FP16 = 512 B a sample, 16 sectors if every corner pair shared one.
 GATHER_CAPTURE = "window2x2_full, 16384 rays (1.99 M samples), --set full"
-MEASURED_GATHER_SECTORS_PER_SAMPLE = {("mixed", True, 1): (65.3, 45.8, GATHER_CAPTURE)}
+MEASURED_GATHER_SECTORS_PER_SAMPLE = {("mixed", True, 1): (65.3, 45.6, GATHER_CAPTURE)}
 
 
 def roofline_of(w, prec_key, name, per_launch_s, units, saved, split, pk, probe=None):
