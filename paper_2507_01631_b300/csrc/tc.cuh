@@ -117,24 +117,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// Bulk copy (not tensor-mapped) of `bytes` from this CTA's shared memory to global, with an L2
-// cache policy, tracked in the issuing thread's bulk async-groups (bulk_commit closes a group).
-// Same alignment rules as bulk_g2s.
-__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes, uint64_t policy) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
-               "r"(smem_u32(src)), "r"(bytes), "l"(policy)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Wait until all but the newest N bulk groups this thread committed have read their
-// shared-memory sources (those sources may then be rewritten).
-template <int N = 0>
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-// Wait until every bulk group this thread committed has completed (its global writes performed).
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
 // Bounded wait for the phase with the given parity that also gives up when *abort
 // becomes non-zero: 0 = completed, 1 = aborted, 2 = gave up after kWaitLimitNs.
 __device__ __forceinline__ int mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, const volatile int *abort) {
@@ -209,20 +191,12 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// Warp-wide: 32 lanes x 8 / 16 consecutive 32-bit columns from registers to tensor memory at
+// Warp-wide: 32 lanes x 8 (or 1) consecutive 32-bit columns from registers to tensor memory at
 // taddr (lane field = the warp's quarter); tcgen05.wait::st (wait_st) before they are read.
 __device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&v)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
                "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
                : "memory");
-}
-__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
 }
 __device__ __forceinline__ void st1(uint32_t taddr, uint32_t v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
