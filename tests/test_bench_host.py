@@ -25,7 +25,7 @@ def test_gather_sectors_cover_the_default_forward_only():
 
 
 def test_method_bytes_of_the_headline_workload_by_hand():
-    """The survey's algorithmic bytes per sample for L = 16 levels x F = 2 features: the gather
+    """The method's algorithmic bytes per sample for L = 16 levels x F = 2 features: the gather
     reads 8 corners x 16 x 2 FP16 = 512 B (binary32 tables: 1024 B), the scatter adds 8 x 16 x 2
     binary32 = 1024 B; the field kernels' streams xyz 12 B in, (sigma, rgb) 16 B out (forward) or
     (dsigma, drgb) 16 B in (backward); the step 512 + 1024 + xyz 12 + t, delta 8 + 16 + 16 = 1588."""
