@@ -58,6 +58,21 @@ def test_roofline_fields_recomputed_by_hand():
     assert abs(r["tensor"]["achieved"] - 2 * 2 * 12480 * units / t / 1e12) < 1e-9
 
 
+def test_forward_roofline_fields_recomputed_by_hand():
+    """The forward's entry: 540 method bytes a sample (512 B gather, xyz 12 B, (sigma, rgb) 16 B)
+    x samples / launch time against the measured peak; its traffic from the forward's own capture;
+    tensor FLOPs 2 x 12,480 a sample; no reduction roofline."""
+    w = W.get("window2x2_full")
+    pk = {"hbm_gbs": 6500.0, "bf16_tflops_sustained": 1400.0, "source": "test"}
+    units, t = 64e6, 0.018
+    r = bench.roofline_of(w, "mixed", "field_forward", t, units, True, 1, pk, {"v4": {"ops_per_s": 200e9}})
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 540 * units / t / 1e9) < 1e-9
+    assert abs(r["frac"] - 540 * units / t / 1e9 / 6500.0) < 1e-12
+    assert abs(r["traffic"] - bench.dram_bytes_per_sample("mixed", "field_forward", True, 1) * units) < 1.0
+    assert abs(r["tensor"]["achieved"] - 2 * 12480 * units / t / 1e12) < 1e-9
+    assert "l2_reduction" not in r
+
+
 def test_algorithmic_work_of_the_headline_workload_by_hand():
     """The implementation's own per-sample work for the 2x2 window (L = 16 levels x F = 2
     features, 64-wide hidden layers, 16-d embedding, colour net), counted by hand from the layer
